@@ -1,0 +1,354 @@
+"""Benchmark of the direct PP N-body hot path on GB300.
+
+Workload (one "step"): one KDK leapfrog step (Eq. 5-7: the O(N^2) force and
+potential sum of Eq. 1-2 plus the fused O(N) update) and the Eq. 8-10
+diagnostics, on the exponential-disk + Plummer-halo model at N = 2^20
+(eps = 0.02, dt = 5e-4, seed 20180113), in binary64 (the headline `value`)
+and in the mixed FP32-pair / FP64-accumulate mode (reported beside it).
+Ginteractions/s counts N^2 pair evaluations per force evaluation (the self
+pair included in the count; 20 flop per interaction where flops are quoted).
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Multi-GPU runs (torchrun) are independent replicas: each rank steps its own
+copy of the workload; value = all ranks' interactions / slowest rank's time.
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of particles of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Ginteractions/s at N=2^20, FP64 vs mixed at stated force error; p99 step latency"
+UNIT = "Ginteractions/s"
+FLOP_PER_INTERACTION = 20
+N_FULL = 2 ** 20
+EPS, DT = 0.02, 5e-4
+SMS, FP64_PER_CLK, FP32_PER_CLK, SM_MAX_GHZ = 152, 2, 128, 2.07
+# derived ALU peaks (flop/s): SMs x lanes-per-clock x 2 (FMA) x max SM clock
+FP64_PEAK_TFLOPS = SMS * FP64_PER_CLK * 2 * SM_MAX_GHZ / 1e3
+FP32_PEAK_TFLOPS = SMS * FP32_PER_CLK * 2 * SM_MAX_GHZ / 1e3
+
+
+def workload_desc(n):
+    return (f"exponential disk (Rd=1, Rmax=5, h=0.05, Q=1.2) + live Plummer halo (a=3), 1:1, "
+            f"N={n}, eps={EPS}, KDK dt={DT}, seed 20180113")
+
+
+# ------------------------------------------------------------------ helpers
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def sample_rows(n, k, seed=7):
+    return np.sort(np.random.default_rng(seed).choice(n, k, replace=False))
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import nbody_ics
+    import oracle
+    w = nbody_ics.workload("disk_halo", n=N_FULL)
+    cores = oracle.max_threads()
+    rows_per_step = args.ref_rows
+    steps = []
+    for k in range(args.warmup + args.steps):
+        rows = sample_rows(N_FULL, rows_per_step, seed=100 + k)
+        t0 = time.perf_counter()
+        oracle.accel(w["pos"], w["mass"], EPS, 1.0, rows=rows, threads=cores)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            steps.append(dt)
+    inter = rows_per_step * N_FULL
+    value = inter / statistics.mean(steps) / 1e9
+    sample = (f"{rows_per_step} sampled i-particles x all {N_FULL} j per step "
+              f"(FP64 oracle, Neumaier sums, OpenMP)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(steps) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(N_FULL), "mode": "fp64", "sample_rows": rows_per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def time_mode(nb, torch, w, mode, args, flush, clocks=None):
+    """W warm-up + K timed KDK steps (with diagnostics) of one simulation.
+    Returns per-step ms, force-kernel ms per launch, launches, diag, sim."""
+    n = len(w["mass"])
+    sim = nb.Simulation(n, mode=mode, eps=EPS)
+    sim.set_state(w["pos"], w["vel"], w["mass"])
+    stream = torch.cuda.current_stream()
+    diag0 = sim.diagnostics()           # a(t0) and E0
+    for _ in range(args.warmup):
+        sim.step(DT, 1)
+        sim.diagnostics()
+    torch.cuda.synchronize()
+    if args.world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sim.profile(True)
+    sim.profile_read()
+    l0 = sim.launch_count
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if clocks:
+        clocks.start()
+    diags = []
+    for k in range(args.steps):
+        flush.zero_()                   # evict L2 (buffer larger than L2) between timed steps
+        ev[k][0].record(stream)
+        sim.step(DT, 1)
+        diags.append(sim.diagnostics())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    launches = sim.launch_count - l0
+    fms, fl = sim.profile_read()
+    sim.profile(False)
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    return dict(per_step=per_step, force_ms=fms / max(fl, 1), force_launches=fl,
+                launches=launches, diag0=diag0, diags=diags, sim=sim, clocks=clk)
+
+
+def e2e_mode(nb, torch, w, mode, steps, warmup):
+    """The Eq. 1-2 force call through the C ABI with pinned host buffers: the
+    H2D copy of positions and masses and the D2H copy of accelerations and
+    potentials are inside the timed region."""
+    import ctypes
+    n = len(w["mass"])
+    pos = torch.tensor(w["pos"]).pin_memory()
+    mass = torch.tensor(w["mass"]).pin_memory()
+    acc = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    pot = torch.empty((n,), dtype=torch.float64).pin_memory()
+    sim = nb.Simulation(n, mode=mode, eps=EPS)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    call = lambda: nb.check(nb.lib.nbody_accel(sim._h, ptr(pos), ptr(mass), ptr(acc), ptr(pot), 0),  # noqa: E731
+                            "nbody_accel")
+    for _ in range(warmup):
+        call()
+    ts = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        call()                          # synchronising: outputs are on the host when it returns
+        ts.append(time.perf_counter() - t0)
+    sim.close()
+    return dict(sec=statistics.mean(ts), h2d=pos.numel() * 8 + mass.numel() * 8,
+                d2h=acc.numel() * 8 + pot.numel() * 8)
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    args.world = world
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import nbody_ics
+    import paper_1803_01190_gb300 as nb
+    n = args.n
+    w = nbody_ics.workload("disk_halo", n=n)
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    clocks = ClockSampler(local)
+    inter = float(n) * n
+
+    fp64 = time_mode(nb, torch, w, "fp64", args, flush, clocks=clocks)
+    mixed = time_mode(nb, torch, w, "mixed", args, flush)
+
+    def agg(per_step):
+        ms = statistics.mean(per_step)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    ms64 = agg(fp64["per_step"])
+    msmx = agg(mixed["per_step"])
+    value = world * inter / (ms64 * 1e-3) / 1e9
+    value_mx = world * inter / (msmx * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers
+    e2e64 = e2e_mode(nb, torch, w, "fp64", steps=args.e2e_steps, warmup=1)
+    e2emx = e2e_mode(nb, torch, w, "mixed", steps=max(args.steps, 3), warmup=args.warmup)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+        return
+
+    # CPU baseline and force error: the oracle on sampled particles of the
+    # current (post-step) state of both runs
+    import oracle
+    cores = oracle.max_threads()
+    p64, _, _, _ = fp64["sim"].get_state()
+    a64, pot64 = fp64["sim"].get_accel()
+    pmx, _, _, _ = mixed["sim"].get_state()
+    amx, _ = mixed["sim"].get_accel()
+    rows = sample_rows(n, args.ref_rows)
+    t0 = time.perf_counter()
+    ao64, po64, smag = oracle.accel(p64, w["mass"], EPS, 1.0, rows=rows, threads=cores)
+    cpu_s = time.perf_counter() - t0
+    aomx, _, _ = oracle.accel(pmx, w["mass"], EPS, 1.0, rows=rows, threads=cores)
+    cpu_value = len(rows) * n / cpu_s / 1e9
+
+    def errs(a, ao):
+        e = np.linalg.norm(a[rows] - ao, axis=1) / np.linalg.norm(ao, axis=1)
+        return {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max())}
+
+    U = 2.0 ** -53
+    gate = np.linalg.norm(a64[rows] - ao64, axis=1) <= (
+        1e-12 * np.linalg.norm(ao64, axis=1) + 4 * U * np.sqrt(n) * smag)
+
+    def drift(d0, ds):
+        E0, P0, L0 = d0["E"], d0["P"], d0["L"][2]
+        return {"dE_over_E0": max(abs(d["E"] / E0 - 1) for d in ds),
+                "dP_abs": max(float(np.linalg.norm(d["P"] - P0)) for d in ds),
+                "dLz_over_Lz0": max(abs(d["L"][2] / L0 - 1) for d in ds)}
+
+    fms = fp64["force_ms"]
+    achieved_tf = inter * FLOP_PER_INTERACTION / (fms * 1e-3) / 1e12
+    per = sorted(fp64["per_step"])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(n), "n": n, "mode": "fp64", "scheme": "kdk",
+                   "l2": "flushed between timed steps (256 MB device write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "launch": fp64["sim"].get_launch()},
+        "p50_step_ms": float(np.percentile(per, 50)), "p99_step_ms": float(np.percentile(per, 99)),
+        "roofline": {"bound": "alu", "kernel": "k_force_f64", "achieved": achieved_tf,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                     "traffic": None,
+                     "flop_convention": f"{FLOP_PER_INTERACTION} flop/interaction x N^2 per launch",
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                     "force_ms_per_launch": fms, "force_share_of_step": fms / ms64},
+        "gpu_launches": fp64["launches"] * world,
+        "clocks": fp64["clocks"],
+        "e2e": {"value": world * inter / e2e64["sec"] / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": e2e64["h2d"], "d2h_bytes_per_step": e2e64["d2h"],
+                "call": "nbody_accel (host pinned buffers), FP64", "steps": args.e2e_steps},
+        "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{len(rows)} sampled i-particles x all {n} j of the FP64 "
+                                   f"state after the timed steps ({cpu_s:.1f} s)"},
+        "force_error_vs_oracle": {"fp64": {**errs(a64, ao64), "gate_1e-12_pass": bool(gate.all())},
+                                  "mixed": errs(amx, aomx), "rows": len(rows)},
+        "mixed": {"value": value_mx, "unit": UNIT, "ms_per_step": msmx,
+                  "speedup_vs_fp64": value_mx / value,
+                  "p50_step_ms": float(np.percentile(mixed["per_step"], 50)),
+                  "p99_step_ms": float(np.percentile(mixed["per_step"], 99)),
+                  "force_ms_per_launch": mixed["force_ms"],
+                  "roofline": {"bound": "alu", "kernel": "k_force_mixed",
+                               "achieved": inter * FLOP_PER_INTERACTION / (mixed["force_ms"] * 1e-3) / 1e12,
+                               "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": inter * FLOP_PER_INTERACTION / (mixed["force_ms"] * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                               "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"},
+                  "e2e": {"value": world * inter / e2emx["sec"] / 1e9, "unit": UNIT},
+                  "gpu_launches": mixed["launches"] * world,
+                  "launch": mixed["sim"].get_launch()},
+        "drift_over_timed_steps": {"fp64": drift(fp64["diag0"], fp64["diags"]),
+                                   "mixed": drift(mixed["diag0"], mixed["diags"])},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_FULL)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--ref-rows", type=int, default=1024)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

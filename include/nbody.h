@@ -1,0 +1,188 @@
+/*
+ * nbody.h -- C ABI of the GB300 direct particle-particle (PP) N-body library.
+ *
+ * The library computes the O(N^2) softened gravitational accelerations and
+ * potentials of Khrapov, Khoperskov & Khoperskov (2018), "New features of
+ * parallel implementation of N-body problems on GPU", and advances them with
+ * the paper's KDK leapfrog or a fourth-order scheme, on one NVIDIA GB300
+ * (sm_103a) GPU.  Every call is plain C: pointers, sizes and codes, no C++ or
+ * framework types.
+ *
+ * Conventions for every function below
+ *   - Return value: NBODY_OK (0) or a negative NBODY_E* code; nothing throws.
+ *     nbody_strerror() turns a code into text; nbody_last_error() gives the
+ *     detail of the most recent failure on the calling thread.
+ *   - Arrays of 3-vectors are n x 3 row-major doubles (x, y, z of particle i
+ *     at [3i], [3i+1], [3i+2]); scalar arrays are n doubles.
+ *   - on_device = 0: the pointers are host memory; on_device = 1: they are
+ *     device memory of the context's GPU.  The caller owns every pointer it
+ *     passes and keeps it valid until the call returns (host pointers) or
+ *     until the context's stream has reached the call (device pointers).
+ *   - A context owns its resident device state and issues all its work on the
+ *     CUDA stream given at creation (NULL = the legacy default stream).
+ *     Calls that return host values synchronise that stream; the others are
+ *     stream-ordered and return before the GPU finishes.
+ *   - A context is not thread-safe; use one per thread or lock around it.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define NBODY_OK        0
+#define NBODY_EINVAL   -1  /* bad argument: n < 1, eps < 0, eps == 0 with mode that needs eps > 0,
+                              non-finite input, dt <= 0 or non-finite, unknown mode or scheme,
+                              NULL pointer */
+#define NBODY_ENOMEM   -2  /* device or host allocation failed */
+#define NBODY_ECUDA    -3  /* a CUDA runtime call or kernel launch failed */
+#define NBODY_ETIMEOUT -4  /* a bounded wait on the GPU expired */
+#define NBODY_ESTATE   -5  /* the call needs state that was never set (nbody_set_state) */
+#define NBODY_ENOSPC   -6  /* a batch has no free slot or not enough reserved memory */
+
+/* ---- precision modes (Eq. 2 evaluated in...) ---------------------------- */
+#define NBODY_FP64  0  /* binary64 throughout: the paper's double precision (DP) */
+#define NBODY_MIXED 1  /* binary32 pair arithmetic on coordinates re-centred per j-tile from
+                          binary64 storage; tile partial sums accumulated with compensation
+                          and returned in binary64; state and update in binary64 */
+#define NBODY_FP32  2  /* binary32 throughout, state included: the paper's single precision (SP) */
+
+/* ---- time integration schemes ------------------------------------------ */
+#define NBODY_KDK 0    /* Eq. 5-7 (section 1): predictor, drift, one force evaluation, corrector */
+#define NBODY_RK4 1    /* the paper's fourth-order scheme (abstract), read as classical
+                          Runge-Kutta on (r, v): four force evaluations per step */
+
+typedef struct nbody_ctx nbody_ctx;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int nbody_version(void);
+
+/* Text for an error code (static storage, never NULL). */
+const char *nbody_strerror(int code);
+
+/* Detail of the last failure on this thread (static per-thread storage). */
+const char *nbody_last_error(void);
+
+/*
+ * Create a simulation context for n particles (Eq. 1: i = 1..n) with
+ * softening eps (the paper's delta, Eq. 2: |r_i - r_j + delta| =
+ * sqrt(|r_i - r_j|^2 + delta^2)) and gravitational constant G, in precision
+ * `mode`, on the current CUDA device, issuing work on `cuda_stream`
+ * (a cudaStream_t, or NULL).  Allocates the resident device state.
+ * eps == 0 is allowed (the self pair j == i is excluded explicitly, Eq. 1);
+ * coincident particles then give non-finite results, as Eq. 2 does.
+ * Errors: EINVAL (n < 1, eps < 0 or non-finite, G non-finite, unknown mode,
+ * out == NULL), ENOMEM, ECUDA.
+ */
+int nbody_create(nbody_ctx **out, int64_t n, int mode, double eps, double G, void *cuda_stream);
+
+/* Free a context and its device memory (synchronises its stream).  NULL is a no-op. */
+int nbody_destroy(nbody_ctx *ctx);
+
+/*
+ * Bound, in seconds, on every host wait of this context (the calls that
+ * synchronise).  0 (the default) waits without limit.  When a wait exceeds
+ * the bound the call returns NBODY_ETIMEOUT; the queued GPU work is not
+ * cancelled, and the context may be used again once it has finished.
+ */
+int nbody_set_timeout(nbody_ctx *ctx, double seconds);
+
+/*
+ * Set positions pos (n x 3), velocities vel (n x 3) and masses mass (n) and
+ * reset the time to 0 and the step counter to 0.  vel may be NULL (zero
+ * velocities).  Inputs are checked: any non-finite value or a negative mass
+ * gives EINVAL and leaves the previous state in place.  Synchronises.
+ */
+int nbody_set_state(nbody_ctx *ctx, const double *pos, const double *vel, const double *mass,
+                    int on_device);
+
+/*
+ * Read the state at the current step boundary: pos (n x 3), vel (n x 3),
+ * the model time *t and the step counter *step.  Any output may be NULL.
+ * Synchronises.  ESTATE before nbody_set_state.
+ */
+int nbody_get_state(nbody_ctx *ctx, double *pos, double *vel, double *t, int64_t *step,
+                    int on_device);
+
+/*
+ * Eq. 1-2 for an arbitrary particle set of the context's size n, in the
+ * context's mode and with its eps and G; does not touch the simulation state:
+ *   acc_i = -G sum_{j != i} m_j (r_i - r_j) / (|r_i - r_j|^2 + eps^2)^{3/2}   (n x 3)
+ *   pot_i = -G sum_{j != i} m_j / (|r_i - r_j|^2 + eps^2)^{1/2}               (n)
+ * pot may be NULL.  Synchronises.  Errors: EINVAL (NULL pos/mass/acc),
+ * ECUDA.  Inputs are not scanned for non-finite values (use set_state for
+ * checked input); a NaN input gives NaN outputs.
+ */
+int nbody_accel(nbody_ctx *ctx, const double *pos, const double *mass, double *acc, double *pot,
+                int on_device);
+
+/*
+ * Accelerations and potentials of the current state (those of the last force
+ * evaluation at the state's positions, computed now if stale).  acc (n x 3),
+ * pot (n); either may be NULL.  Synchronises.
+ */
+int nbody_get_accel(nbody_ctx *ctx, double *acc, double *pot, int on_device);
+
+/*
+ * Advance the state nsteps steps of size dt with `scheme` (NBODY_KDK: Eq. 5-7;
+ * NBODY_RK4: classical Runge-Kutta).  KDK needs a(t) before its first step
+ * (Eq. 5): it is evaluated once when stale, so nsteps KDK steps cost
+ * nsteps + 1 force evaluations the first time and nsteps afterwards.
+ * Stream-ordered: returns once the work is queued.
+ * Errors: EINVAL (unknown scheme, dt <= 0 or non-finite, nsteps < 0),
+ * ESTATE, ECUDA.
+ */
+int nbody_step(nbody_ctx *ctx, int scheme, double dt, int64_t nsteps);
+
+/*
+ * Eq. 8-10 at the current state, reduced on the GPU in binary64 in a fixed
+ * order (deterministic):
+ *   *E  = sum_i m_i |v_i|^2 / 2 - 1/2 sum_i sum_{j != i} G m_i m_j / |r_i - r_j + eps|
+ *         (Eq. 8 prints the potential term with a + sign; a bound system has
+ *          negative potential energy, so it is taken with a - sign here)
+ *   P   = sum_i m_i v_i                            (Eq. 9; 3 doubles)
+ *   L   = sum_i m_i r_i x v_i                      (3 doubles; L[2] is Eq. 10)
+ * Any output may be NULL.  K and W separately: nbody_diagnostics_ext.
+ * Synchronises.
+ */
+int nbody_diagnostics(nbody_ctx *ctx, double *E, double *P, double *L);
+
+/* As nbody_diagnostics, plus kinetic energy *K and potential energy *W (E = K + W). */
+int nbody_diagnostics_ext(nbody_ctx *ctx, double *E, double *K, double *W, double *P, double *L);
+
+/*
+ * Force-kernel launch shape (for tuning; 0 = library default for that field):
+ *   ipt    -- i-particles held in registers per thread (1, 2, 4 or 8)
+ *   jsplit -- number of j-segments evaluated by separate thread blocks and
+ *             summed afterwards in a fixed order (1..64)
+ * The shape changes rounding order only.  EINVAL for unsupported values.
+ */
+int nbody_set_launch(nbody_ctx *ctx, int ipt, int jsplit);
+
+/* Current launch shape actually used for this context's n (outputs may be NULL). */
+int nbody_get_launch(nbody_ctx *ctx, int *ipt, int *jsplit, int *threads, int *tile);
+
+/* Number of kernel launches this context has issued since creation. */
+int64_t nbody_launch_count(const nbody_ctx *ctx);
+
+/*
+ * Opt-in timing of the force kernel (Eq. 1-2 sum, the O(N^2) part): when
+ * enabled, every force-kernel launch is bracketed by two CUDA events recorded
+ * on the context's stream.  nbody_profile_read synchronises, returns the
+ * summed event time in milliseconds and the number of timed launches since
+ * the last read (or since enabling), and resets both.  Either output may be
+ * NULL.  Disabled by default.
+ */
+int nbody_profile(nbody_ctx *ctx, int enable);
+int nbody_profile_read(nbody_ctx *ctx, double *force_ms, int64_t *force_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBODY_H */

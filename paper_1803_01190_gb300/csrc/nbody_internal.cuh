@@ -1,0 +1,100 @@
+// Internal declarations of the GB300 direct-summation N-body library.
+//
+// Device layout of one simulation (n particles, all arrays length n unless
+// stated; `real` is double for FP64/MIXED and float for FP32):
+//   posm[2]  real4 (x, y, z, m)   ping-pong positions+mass; posm[cur] is the
+//                                 state at the step boundary, posm[nxt] the
+//                                 positions of the next force evaluation
+//   vel      real4 (vx, vy, vz, -) velocity at the step boundary
+//   vbar     real4                 KDK half-sum (v + vt)/2 of Eq. 5/7
+//   acc      real4 (ax, ay, az, pot) Eq. 1-2 at posm[cur]
+//   part     real4 x S x n         j-segment partial sums of the force kernel
+//   rk_*     real4                 RK4 stage velocity and running sums
+//   fpos     float4 x n, anchor    MIXED only: j coordinates re-centred per tile
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nbody.h"
+
+namespace nb {
+
+struct __align__(32) d4 {
+  double x, y, z, w;
+};
+
+template <typename real>
+struct vec4;
+template <>
+struct vec4<double> {
+  using type = d4;
+};
+template <>
+struct vec4<float> {
+  using type = float4;
+};
+template <typename real>
+using real4 = typename vec4<real>::type;
+
+// Force-kernel shape.  BT threads per block, R i-particles per thread, T
+// j-particles per shared-memory tile; grid = (ceil(n / (BT*R)), S).
+struct Shape {
+  int bt = 128;
+  int r = 4;
+  int t = 128;
+  int s = 1;
+};
+
+// Raw force sums written by the force kernels, per j-segment s:
+//   part[s*n + i] = ( sum_j m_j (x_j - x_i) / w_ij, ..y.., ..z..,
+//                     sum_j m_j / sqrt(|d_ij|^2 + eps^2) )
+// over j != i in segment s.  G and the sign of the potential are applied by
+// the epilogue kernels.
+struct ForceIn {
+  const void *posm;      // real4 (FP64, FP32) or d4 (MIXED) positions+mass
+  const float4 *fpos;    // MIXED: re-centred j coordinates + float mass
+  const float4 *anchor;  // MIXED: per tile (hi.xyz, lo.xyz) float-float anchors, 2 per tile
+  int64_t n;
+  double eps2;
+  int64_t seg;           // j-segment length (multiple of the tile)
+  void *part;            // S * n entries
+};
+
+// launchers (force.cu); return cudaError_t of the launch
+cudaError_t launch_force(int mode, const ForceIn &in, const Shape &sh, cudaStream_t st);
+cudaError_t launch_mixed_prep(const d4 *posm, int64_t n, int tile, float4 *fpos, float4 *anchor,
+                              cudaStream_t st);
+int force_max_blocks_per_sm(int mode, const Shape &sh);
+bool shape_supported(int mode, const Shape &sh);
+
+// update / epilogue kernels (update.cu)
+struct EpiIn {
+  int64_t n;
+  int S;
+  const void *part;  // S * n raw sums (real4 for FP64/FP32; d4 for MIXED)
+  double G;
+};
+cudaError_t launch_pack(int mode, const double *pos, const double *vel, const double *mass,
+                        int64_t n, void *posm, void *velv, int *flag, cudaStream_t st);
+cudaError_t launch_unpack_state(int mode, const void *posm, const void *velv, int64_t n,
+                                double *pos, double *vel, cudaStream_t st);
+cudaError_t launch_store_acc(int mode, const EpiIn &e, void *acc, cudaStream_t st);
+cudaError_t launch_unpack_acc(int mode, const void *acc, int64_t n, double *acc3, double *pot,
+                              cudaStream_t st);
+cudaError_t launch_kdk_predict(int mode, int64_t n, double dt, const void *posm_cur,
+                               const void *vel, const void *acc, void *vbar, void *posm_nxt,
+                               cudaStream_t st);
+cudaError_t launch_kdk_correct_predict(int mode, const EpiIn &e, double dt, void *acc,
+                                       void *posm_new, void *vel, void *vbar, void *posm_pred,
+                                       cudaStream_t st);
+cudaError_t launch_rk4_stage(int mode, const EpiIn &e, int stage, double dt, const void *posm0,
+                             void *vel0, void *rk_vs, void *rk_sr, void *rk_sv, void *posm_stage,
+                             void *acc, cudaStream_t st);
+cudaError_t launch_diag(int mode, const void *posm, const void *vel, const void *acc, int64_t n,
+                        double *blocks, int nblocks, double *out9, cudaStream_t st);
+int diag_blocks(int64_t n);
+
+inline size_t real_bytes(int mode) { return mode == NBODY_FP32 ? sizeof(float) : sizeof(double); }
+
+}  // namespace nb

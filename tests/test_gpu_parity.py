@@ -1,0 +1,300 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+FP64: element-wise within the gate of tests/gates.py (1e-12 relative plus
+the rounding floor of a reordered binary64 sum).  MIXED and FP32: the error
+against the oracle is measured and bounded (no exact pin exists for reduced
+precision).  Sizes span several tiles and ragged tails; the full-size
+workloads are checked on sampled particles.
+"""
+import numpy as np
+import pytest
+
+import nbody_ics
+import oracle
+from tests.gates import U, fp64_accel_gate, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_1803_01190_gb300 as m
+    return m
+
+
+def _check_fp64(acc, pot, pos, mass, eps, G=1.0, rows=None):
+    acc_o, pot_o, smag = oracle.accel(pos, mass, eps, G, rows=rows)
+    a = acc if rows is None else acc[rows]
+    p = pot if rows is None else pot[rows]
+    ok, err, amag = fp64_accel_gate(a, acc_o, smag, len(mass))
+    assert ok.all(), (err[~ok][:5], amag[~ok][:5])
+    assert np.all(np.abs(p - pot_o) <= 1e-12 * np.abs(pot_o) + 1e-300)
+    return err / np.maximum(amag, 1e-300)
+
+
+# ------------------------------------------------------------------ FP64 force, Eq. 1-2
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 127, 128, 129, 513, 1000, 4096, 5003])
+@pytest.mark.parametrize("eps", [0.01, 0.0])
+def test_fp64_accel_sizes(nb, n, eps):
+    pos, _, _ = nbody_ics.plummer(n, 11 + n)
+    mass = nbody_ics.lognormal_masses(n, 12 + n)
+    with nb.Simulation(n, "fp64", eps=eps, G=1.3) as sim:
+        acc, pot = sim.accel(pos, mass)
+    if n == 1:
+        assert np.all(acc == 0) and np.all(pot == 0)
+        return
+    _check_fp64(acc, pot, pos, mass, eps, 1.3)
+
+
+@pytest.mark.parametrize("ipt", [1, 2, 4, 8])
+@pytest.mark.parametrize("jsplit", [1, 3, 7, 64])
+def test_fp64_launch_shapes(nb, ipt, jsplit):
+    n = 3001
+    w = nbody_ics.workload("plummer", n=n)
+    with nb.Simulation(n, "fp64", eps=w["eps"]) as sim:
+        sim.set_launch(ipt, jsplit)
+        sh = sim.get_launch()
+        assert sh["ipt"] == ipt and 1 <= sh["jsplit"] <= jsplit
+        acc, pot = sim.accel(w["pos"], w["mass"])
+    _check_fp64(acc, pot, w["pos"], w["mass"], w["eps"])
+
+
+def test_fp64_device_pointers(nb):
+    import torch
+    n = 2000
+    w = nbody_ics.workload("plummer", n=n)
+    pos = torch.tensor(w["pos"], device="cuda")
+    mass = torch.tensor(w["mass"], device="cuda")
+    with nb.Simulation(n, "fp64", eps=w["eps"]) as sim:
+        acc, pot = sim.accel(pos, mass)
+    assert acc.is_cuda and pot.is_cuda
+    _check_fp64(acc.cpu().numpy(), pot.cpu().numpy(), w["pos"], w["mass"], w["eps"])
+
+
+def test_fp64_newton_third_law(nb):
+    n = 4096
+    w = nbody_ics.workload("sweep_uniform", n=n)
+    with nb.Simulation(n, "fp64", eps=1e-3) as sim:
+        acc, _ = sim.accel(w["pos"], w["mass"])
+    _, _, smag = oracle.accel(w["pos"], w["mass"], 1e-3)
+    tot = (w["mass"][:, None] * acc).sum(0)
+    assert np.all(np.abs(tot) <= 64 * U * np.sqrt(n) * (w["mass"] * smag).sum())
+
+
+def test_fp64_deterministic(nb):
+    n = 5000
+    w = nbody_ics.workload("plummer", n=n)
+    with nb.Simulation(n, "fp64", eps=w["eps"]) as sim:
+        a1, p1 = sim.accel(w["pos"], w["mass"])
+        a2, p2 = sim.accel(w["pos"], w["mass"])
+    assert np.array_equal(a1, a2) and np.array_equal(p1, p2)
+
+
+def test_golden_fixture(nb):
+    from tests.test_oracle_pins import load_golden
+    g = load_golden()
+    n = len(g["mass"])
+    with nb.Simulation(n, "fp64", eps=g["eps"], G=g["G"]) as sim:
+        sim.set_state(g["pos"], g["vel"], g["mass"])
+        acc, pot = sim.get_accel()
+        d = sim.diagnostics()
+        sim.step(g["dt"], 10, "kdk")
+        kp, kv, _, _ = sim.get_state()
+        sim.set_state(g["pos"], g["vel"], g["mass"])
+        sim.step(g["dt"], 3, "rk4")
+        rp, rv, _, _ = sim.get_state()
+    _, _, smag = oracle.accel(g["pos"], g["mass"], g["eps"])
+    assert fp64_accel_gate(acc, g["acc"], smag, n)[0].all()
+    assert np.allclose(pot, g["pot"], rtol=1e-12, atol=0)
+    scale = np.abs(g["pos"]).max()
+    vscale = np.abs(g["vel"]).max()
+    assert np.abs(kp - g["kdk_pos"]).max() <= 1e-12 * scale
+    assert np.abs(kv - g["kdk_vel"]).max() <= 1e-12 * vscale
+    assert np.abs(rp - g["rk4_pos"]).max() <= 1e-12 * scale
+    assert np.abs(rv - g["rk4_vel"]).max() <= 1e-12 * vscale
+    assert abs(d["E"] - g["diag"][0]) <= 1e-13 * abs(g["diag"][0])
+
+
+# ------------------------------------------------------------------ KDK, Eq. 5-7 (Plummer N=4096)
+def test_fp64_kdk_plummer4096_each_step(nb):
+    """Plummer N=4096, eps=0.01, 10 KDK steps of dt=1e-3: a, pot, r, v and
+    E, P, L compared with the oracle after every step."""
+    w = nbody_ics.workload("plummer")
+    pos, vel, mass, eps = w["pos"], w["vel"], w["mass"], w["eps"]
+    n = len(mass)
+    dt = 1e-3
+    op, ov = pos.copy(), vel.copy()
+    oa = None
+    with nb.Simulation(n, "fp64", eps=eps) as sim:
+        sim.set_state(pos, vel, mass)
+        for k in range(10):
+            sim.step(dt, 1)
+            op, ov, oa, opot = oracle.kdk(op, ov, mass, eps, 1.0, dt, 1, acc0=oa)
+            p, v, t, s = sim.get_state()
+            acc, pot = sim.get_accel()
+            assert s == k + 1 and abs(t - (k + 1) * dt) < 1e-15
+            assert np.abs(p - op).max() <= 1e-12 * np.abs(op).max()
+            assert np.abs(v - ov).max() <= 1e-12 * np.abs(ov).max()
+            _, _, smag = oracle.accel(op, mass, eps)
+            assert fp64_accel_gate(acc, oa, smag, n)[0].all()
+            assert np.all(np.abs(pot - opot) <= 1e-12 * np.abs(opot))
+            d = sim.diagnostics()
+            od = oracle.diag(op, ov, mass, eps)
+            assert abs(d["E"] - od["E"]) <= 1e-12 * abs(od["E"])
+            assert np.abs(d["P"] - od["P"]).max() <= 1e-15
+            assert np.abs(d["L"] - od["L"]).max() <= 1e-14
+
+
+def test_fp64_kdk_multistep_equals_single_steps(nb):
+    w = nbody_ics.workload("plummer", n=1500)
+    with nb.Simulation(1500, "fp64", eps=0.01) as a, nb.Simulation(1500, "fp64", eps=0.01) as b:
+        a.set_state(w["pos"], w["vel"], w["mass"])
+        b.set_state(w["pos"], w["vel"], w["mass"])
+        a.step(1e-3, 7)
+        for _ in range(7):
+            b.step(1e-3, 1)
+        pa, va, _, _ = a.get_state()
+        pb, vb, _, _ = b.get_state()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+
+
+def test_fp64_rk4(nb):
+    w = nbody_ics.workload("plummer", n=1000)
+    with nb.Simulation(1000, "fp64", eps=0.01) as sim:
+        sim.set_state(w["pos"], w["vel"], w["mass"])
+        sim.step(2e-3, 4, "rk4")
+        p, v, t, s = sim.get_state()
+        acc, _ = sim.get_accel()
+    op, ov, oa = oracle.rk4(w["pos"], w["vel"], w["mass"], 0.01, 1.0, 2e-3, 4)
+    assert s == 4
+    assert np.abs(p - op).max() <= 1e-12 * np.abs(op).max()
+    assert np.abs(v - ov).max() <= 1e-12 * np.abs(ov).max()
+    _, _, smag = oracle.accel(op, w["mass"], 0.01)
+    assert fp64_accel_gate(acc, oa, smag, 1000)[0].all()
+
+
+def test_kdk_then_rk4_then_kdk(nb):
+    """Switching schemes keeps the state consistent (a(t) recomputed when stale)."""
+    w = nbody_ics.workload("plummer", n=700)
+    args = (w["mass"], 0.02, 1.0)
+    with nb.Simulation(700, "fp64", eps=0.02) as sim:
+        sim.set_state(w["pos"], w["vel"], w["mass"])
+        sim.step(1e-3, 2, "kdk")
+        sim.step(1e-3, 1, "rk4")
+        sim.step(2e-3, 2, "kdk")
+        p, v, t, s = sim.get_state()
+    op, ov, _, _ = oracle.kdk(w["pos"], w["vel"], *args, 1e-3, 2)
+    op, ov, _ = oracle.rk4(op, ov, *args, 1e-3, 1)
+    op, ov, _, _ = oracle.kdk(op, ov, *args, 2e-3, 2)
+    assert s == 5 and abs(t - 7e-3) < 1e-15
+    assert np.abs(p - op).max() <= 1e-12 * np.abs(op).max()
+    assert np.abs(v - ov).max() <= 1e-12 * np.abs(ov).max()
+
+
+# ------------------------------------------------------------------ state handling
+def test_set_state_rejects_non_finite(nb):
+    w = nbody_ics.workload("plummer", n=300)
+    with nb.Simulation(300, "fp64", eps=0.01) as sim:
+        sim.set_state(w["pos"], w["vel"], w["mass"])
+        bad = w["pos"].copy()
+        bad[17, 1] = np.nan
+        with pytest.raises(nb.NbodyError) as e:
+            sim.set_state(bad, w["vel"], w["mass"])
+        assert e.value.code == -1
+        badm = w["mass"].copy()
+        badm[3] = -1.0
+        with pytest.raises(nb.NbodyError):
+            sim.set_state(w["pos"], w["vel"], badm)
+        p, v, _, _ = sim.get_state()  # previous state kept
+        assert np.array_equal(p, w["pos"]) and np.array_equal(v, w["vel"])
+
+
+def test_errors_before_state(nb):
+    with nb.Simulation(10, "fp64", eps=0.01) as sim:
+        with pytest.raises(nb.NbodyError) as e:
+            sim.step(1e-3, 1)
+        assert e.value.code == -5
+        with pytest.raises(nb.NbodyError) as e:
+            sim.step(-1e-3, 1)
+        assert e.value.code == -1
+
+
+# ------------------------------------------------------------------ reduced precision (measured)
+def _measured(nb, mode, name, n, rows=512, seed=3):
+    w = nbody_ics.workload(name, n=n)
+    g = np.random.default_rng(seed)
+    r = np.sort(g.choice(n, min(rows, n), replace=False))
+    with nb.Simulation(n, mode, eps=w["eps"]) as sim:
+        acc, pot = sim.accel(w["pos"], w["mass"])
+    acc_o, pot_o, _ = oracle.accel(w["pos"], w["mass"], w["eps"], rows=r)
+    e = rel_errors(acc[r], acc_o)
+    ep = np.abs(pot[r] - pot_o) / np.abs(pot_o)
+    return np.sqrt((e ** 2).mean()), e.max(), ep.max()
+
+
+@pytest.mark.parametrize("n", [1000, 2 ** 14 + 7])
+def test_mixed_force_error(nb, n):
+    rms, mx, pmx = _measured(nb, "mixed", "disk_halo", n)
+    print(f"mixed N={n}: rms {rms:.2e} max {mx:.2e} pot max {pmx:.2e}")
+    assert rms <= 1e-6 and mx <= 2e-5 and pmx <= 1e-6
+
+
+@pytest.mark.parametrize("n", [1000, 2 ** 14 + 7])
+def test_fp32_force_error(nb, n):
+    rms, mx, pmx = _measured(nb, "fp32", "disk_halo", n)
+    print(f"fp32 N={n}: rms {rms:.2e} max {mx:.2e} pot max {pmx:.2e}")
+    assert rms <= 1e-4 and mx <= 1e-3
+
+
+def test_mixed_kdk_tracks_fp64(nb):
+    """Mixed state stays binary64; after 20 KDK steps it is within the force
+    error's effect of the oracle trajectory."""
+    w = nbody_ics.workload("plummer", n=2048)
+    with nb.Simulation(2048, "mixed", eps=0.01) as sim:
+        sim.set_state(w["pos"], w["vel"], w["mass"])
+        sim.step(1e-3, 20)
+        p, v, _, _ = sim.get_state()
+        d = sim.diagnostics()
+    op, ov, _, _ = oracle.kdk(w["pos"], w["vel"], w["mass"], 0.01, 1.0, 1e-3, 20)
+    od = oracle.diag(op, ov, w["mass"], 0.01)
+    assert np.abs(p - op).max() <= 1e-9 * np.abs(op).max()
+    assert np.abs(v - ov).max() <= 1e-6 * np.abs(ov).max()
+    assert abs(d["E"] / od["E"] - 1) <= 1e-6
+
+
+# ------------------------------------------------------------------ full-size workloads (sampled)
+@pytest.mark.slow
+def test_fp64_disk_halo_2_17_sampled(nb):
+    w = nbody_ics.workload("disk_halo", n=2 ** 17)
+    n = 2 ** 17
+    rows = np.concatenate([np.arange(0, 64), np.arange(n - 64, n),
+                           np.random.default_rng(0).choice(n, 128, replace=False)])
+    with nb.Simulation(n, "fp64", eps=w["eps"]) as sim:
+        acc, pot = sim.accel(w["pos"], w["mass"])
+    _check_fp64(acc, pot, w["pos"], w["mass"], w["eps"], rows=rows)
+
+
+@pytest.mark.slow
+def test_fp64_and_mixed_disk_halo_2_20_sampled(nb):
+    """The benchmark's workload (disk + halo, N = 2^20, eps = 0.02) in the
+    default launch shape: FP64 on sampled particles within the FP64 gate,
+    mixed RMS error <= 1e-6 on the same sample."""
+    n = 2 ** 20
+    w = nbody_ics.workload("disk_halo", n=n)
+    rows = np.concatenate([np.arange(0, 32), np.arange(n - 32, n),
+                           np.random.default_rng(1).choice(n, 64, replace=False)])
+    acc_o, pot_o, smag = oracle.accel(w["pos"], w["mass"], w["eps"], rows=rows)
+    with nb.Simulation(n, "mixed", eps=w["eps"]) as sim:
+        accm, _ = sim.accel(w["pos"], w["mass"])
+    e = rel_errors(accm[rows], acc_o)
+    assert np.sqrt((e ** 2).mean()) <= 1e-6
+    with nb.Simulation(n, "fp64", eps=w["eps"]) as sim:
+        acc, pot = sim.accel(w["pos"], w["mass"])
+    ok, err, amag = fp64_accel_gate(acc[rows], acc_o, smag, n)
+    assert ok.all()
+    assert np.all(np.abs(pot[rows] - pot_o) <= 1e-12 * np.abs(pot_o))
