@@ -24,8 +24,8 @@
 //         its seed from the binary32 special-function unit through integer
 //         bit moves (no FP64 conversion instruction) and refines it with one
 //         third-order step in binary64.
-//   mixed binary32 pair arithmetic on coordinates re-centred on an anchor per
-//         j-tile, with the i coordinates held as float-float pairs so that the
+//   mixed binary32 pair arithmetic on coordinates re-centred on an anchor (the
+//         per-coordinate median) per j-tile, with the i coordinates held as float-float pairs so that the
 //         per-tile shift costs three binary32 operations per coordinate and no
 //         FP64 instruction; per-tile binary32 partial sums are folded into
 //         float-float (compensated, TwoSum) accumulators, returned as binary64.
@@ -257,53 +257,57 @@ __global__ void __launch_bounds__(BT) k_force_mixed(const d4 *__restrict__ posm,
   }
 }
 
-// One block per j-tile: anchor c = centre of the tile's bounding box (binary64),
-// fpos[j] = float(r_j - c), float(m_j); anchor[2t], anchor[2t+1] = float-float c.
+// One block per j-tile: anchor c = the per-coordinate median of the tile's
+// positions (binary64), fpos[j] = float(r_j - c), float(m_j); anchor[2t],
+// anchor[2t+1] = float-float c.  The median follows the bulk of the tile: for
+// a spatially compact tile it lies inside it, and for an unsorted tile it
+// stays near the centre of the particle distribution even when a few members
+// sit far out in a halo (a bounding-box centre would be pulled out there and
+// cost every coordinate relative to it several digits).  It is found with a
+// bitonic sort of each coordinate in shared memory (tile = block = 256).
 template <int BT>
 __global__ void __launch_bounds__(BT) k_mixed_prep(const d4 *__restrict__ posm, int64_t n,
                                                    int tile, float4 *__restrict__ fpos,
                                                    float4 *__restrict__ anchor) {
-  __shared__ double smin[3][BT], smax[3][BT];
+  static_assert((BT & (BT - 1)) == 0, "bitonic sort needs a power-of-two block");
+  __shared__ double v[BT];
   const int64_t t = blockIdx.x;
   const int64_t j0 = t * tile;
   const int cnt = (int)min((int64_t)tile, n - j0);
-  double lo[3] = {1e308, 1e308, 1e308}, hi[3] = {-1e308, -1e308, -1e308};
-  for (int k = threadIdx.x; k < cnt; k += BT) {
-    const d4 p = posm[j0 + k];
-    lo[0] = fmin(lo[0], p.x);
-    hi[0] = fmax(hi[0], p.x);
-    lo[1] = fmin(lo[1], p.y);
-    hi[1] = fmax(hi[1], p.y);
-    lo[2] = fmin(lo[2], p.z);
-    hi[2] = fmax(hi[2], p.z);
-  }
-  for (int c = 0; c < 3; c++) {
-    smin[c][threadIdx.x] = lo[c];
-    smax[c][threadIdx.x] = hi[c];
-  }
-  __syncthreads();
-  for (int w = BT / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int c = 0; c < 3; c++) {
-        smin[c][threadIdx.x] = fmin(smin[c][threadIdx.x], smin[c][threadIdx.x + w]);
-        smax[c][threadIdx.x] = fmax(smax[c][threadIdx.x], smax[c][threadIdx.x + w]);
-      }
+  const int tid = threadIdx.x;
+  d4 p = {0, 0, 0, 0};
+  if (tid < cnt) p = posm[j0 + tid];
+  double c[3];
+  for (int q = 0; q < 3; q++) {
     __syncthreads();
+    v[tid] = tid < cnt ? (q == 0 ? p.x : q == 1 ? p.y : p.z) : 1e308;
+    __syncthreads();
+    for (int k = 2; k <= BT; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const int o = tid ^ j;
+        if (o > tid) {
+          const double a = v[tid], b = v[o];
+          const bool up = (tid & k) == 0;
+          if ((a > b) == up) {
+            v[tid] = b;
+            v[o] = a;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    c[q] = v[(cnt - 1) / 2];
   }
-  const double cx = 0.5 * (smin[0][0] + smax[0][0]);
-  const double cy = 0.5 * (smin[1][0] + smax[1][0]);
-  const double cz = 0.5 * (smin[2][0] + smax[2][0]);
-  for (int k = threadIdx.x; k < cnt; k += BT) {
-    const d4 p = posm[j0 + k];
-    fpos[j0 + k] = make_float4(__double2float_rn(p.x - cx), __double2float_rn(p.y - cy),
-                               __double2float_rn(p.z - cz), __double2float_rn(p.w));
-  }
-  if (threadIdx.x == 0) {
-    const float hx = __double2float_rn(cx), hy = __double2float_rn(cy), hz = __double2float_rn(cz);
+  if (tid < cnt)
+    fpos[j0 + tid] = make_float4(__double2float_rn(p.x - c[0]), __double2float_rn(p.y - c[1]),
+                                 __double2float_rn(p.z - c[2]), __double2float_rn(p.w));
+  if (tid == 0) {
+    const float hx = __double2float_rn(c[0]), hy = __double2float_rn(c[1]),
+                hz = __double2float_rn(c[2]);
     anchor[2 * t] = make_float4(hx, hy, hz, 0.0f);
-    anchor[2 * t + 1] = make_float4(__double2float_rn(cx - (double)hx),
-                                    __double2float_rn(cy - (double)hy),
-                                    __double2float_rn(cz - (double)hz), 0.0f);
+    anchor[2 * t + 1] = make_float4(__double2float_rn(c[0] - (double)hx),
+                                    __double2float_rn(c[1] - (double)hy),
+                                    __double2float_rn(c[2] - (double)hz), 0.0f);
   }
 }
 
@@ -429,6 +433,7 @@ cudaError_t launch_force(int mode, const ForceIn &in, const Shape &sh, cudaStrea
 
 cudaError_t launch_mixed_prep(const d4 *posm, int64_t n, int tile, float4 *fpos, float4 *anchor,
                               cudaStream_t st) {
+  if (tile != 256) return cudaErrorInvalidValue;  // one thread per tile member
   const int64_t nt = (n + tile - 1) / tile;
   k_mixed_prep<256><<<(unsigned)nt, 256, 0, st>>>(posm, n, tile, fpos, anchor);
   return cudaGetLastError();
