@@ -181,6 +181,33 @@ int64_t nbody_launch_count(const nbody_ctx *ctx);
 int nbody_profile(nbody_ctx *ctx, int enable);
 int nbody_profile_read(nbody_ctx *ctx, double *force_ms, int64_t *force_launches);
 
+/*
+ * Allocation-free variant of the binary64 force evaluation: the same Eq. 1-2
+ * result as nbody_accel on an NBODY_FP64 context (acc n x 3, pot n, same
+ * kernel), but with no context and no device allocation by the library, for
+ * callers that cannot let it call cudaMalloc: an application that owns all GPU
+ * memory through its own allocator (or has reserved it), or a timing-critical
+ * loop where an allocation or free would stall the device.  The paper has no
+ * counterpart of this entry point.
+ *   pos (n x 3), mass (n), acc (n x 3), pot (n, may be NULL): device pointers
+ *   owned by the caller; work is queued on cuda_stream (NULL = default stream)
+ *   and the call returns before it finishes.
+ * Scratch: one file-scope device array of NBODY_STATIC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits; it limits n to
+ * NBODY_STATIC_MAX_N, and a larger n returns NBODY_EINVAL before any launch.
+ * All calls share that array (nothing in it needs clearing between calls), so
+ * calls whose work overlaps on the GPU (several streams or host threads) race
+ * and give wrong results: order them on one stream.  The first call on each
+ * device looks up the array's device address with that device current; make
+ * that first call before any stream capture begins.
+ * Errors: EINVAL (n < 1, n > NBODY_STATIC_MAX_N, NULL pos/mass/acc, eps < 0 or
+ * non-finite, G non-finite), ECUDA.
+ */
+#define NBODY_STATIC_MAX_N 32768
+#define NBODY_STATIC_SCRATCH_BYTES (16 * 1024 * 1024)
+int nbody_accel_f64_static(int64_t n, const double *pos, const double *mass, double eps, double G,
+                           double *acc, double *pot, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
