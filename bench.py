@@ -214,6 +214,28 @@ def e2e_mode(nb, torch, w, mode, steps, warmup):
                 d2h=acc.numel() * 8 + pot.numel() * 8)
 
 
+def run_serving(args):
+    """Serving workload: Poisson arrivals (200/s) of independent Plummer or
+    disk + halo simulations, N log-uniform in [2^10, 2^16], FP64 or MIXED
+    50/50, 100 KDK steps each, through the continuous-batching server for a
+    bounded wall-clock window.  Offered load (~1e13 interactions/s) exceeds
+    one GPU, so the queue grows; reported: per-mode tick (= per-step)
+    latency p50/p99, aggregate throughput, admitted/completed/queued."""
+    from paper_1803_01190_gb300 import serve
+    reqs = serve.poisson_requests(int(200 * args.serve_seconds) + 1, rate=200.0, seed=20180115,
+                                  nsteps=100, dt=DT)
+    srv = serve.Server(capacity={"fp64": 2 ** 20, "mixed": 2 ** 22},
+                       max_sims={"fp64": 16, "mixed": 64}, autotune=True, keep_state=False)
+    out = srv.run(reqs, duration=args.serve_seconds)
+    srv.close()
+    out.pop("done")
+    out["workload"] = ("Poisson 200 req/s; N log-uniform [2^10, 2^16]; Plummer (eps 0.01) or disk+halo "
+                       "(eps 0.02) 50/50; FP64 or mixed 50/50; 100 KDK steps dt=5e-4; seed 20180115")
+    out["pools"] = {"fp64": {"capacity": 2 ** 20, "max_sims": 16},
+                    "mixed": {"capacity": 2 ** 22, "max_sims": 64}}
+    return out
+
+
 def run_gpu(args):
     import torch
     world, rank, local = dist_setup(args)
@@ -248,6 +270,7 @@ def run_gpu(args):
     # end to end through the C ABI with host buffers
     e2e64 = e2e_mode(nb, torch, w, "fp64", steps=args.e2e_steps, warmup=1)
     e2emx = e2e_mode(nb, torch, w, "mixed", steps=max(args.steps, 3), warmup=args.warmup)
+    serving = run_serving(args) if args.serve_seconds > 0 else None
 
     if rank != 0:
         if world > 1:
@@ -326,6 +349,7 @@ def run_gpu(args):
                   "launch": mixed["sim"].get_launch()},
         "drift_over_timed_steps": {"fp64": drift(fp64["diag0"], fp64["diags"]),
                                    "mixed": drift(mixed["diag0"], mixed["diags"])},
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -341,6 +365,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_FULL)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--ref-rows", type=int, default=1024)
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -181,6 +181,103 @@ int64_t nbody_launch_count(const nbody_ctx *ctx);
 int nbody_profile(nbody_ctx *ctx, int enable);
 int nbody_profile_read(nbody_ctx *ctx, double *force_ms, int64_t *force_launches);
 
+/* ======================================================================
+ * Batched execution of many independent simulations (serving).
+ *
+ * A batch is a device pool of `capacity` particles shared by up to
+ * `max_sims` resident simulations of uneven size.  Each simulation runs the
+ * KDK leapfrog of Eq. 5-7 over the Eq. 1-2 force sum with its own n, eps, G,
+ * dt and mode (NBODY_FP64 or NBODY_MIXED; NBODY_FP32 is not offered here).
+ * One tick (nbody_batch_step) advances every resident simulation by one
+ * step in a few launches whose thread blocks are work units of single
+ * simulations, so small and large simulations share the GPU.  A simulation's
+ * first tick after admission evaluates a(t0) (Eq. 5 needs it) and does not
+ * count as a step.  Results of one simulation do not depend on which others
+ * share its ticks beyond the summation-order effect of the launch shape.
+ * All work is ordered on the stream given at creation; calls that return
+ * host values synchronise it.  The paper runs one system at a time; this
+ * interface is the library's own.
+ * ====================================================================== */
+typedef struct nbody_batch nbody_batch;
+
+/* Device bytes the pool reserves per particle of capacity. */
+int64_t nbody_batch_bytes_per_particle(void);
+
+/* Text of the last batch failure on this thread. */
+const char *nbody_batch_last_error(void);
+
+/* Create a pool (allocates capacity x nbody_batch_bytes_per_particle() bytes).
+ * Errors: EINVAL (capacity < 1, max_sims < 1), ENOMEM, ECUDA. */
+int nbody_batch_create(nbody_batch **out, int64_t capacity, int max_sims, void *cuda_stream);
+int nbody_batch_destroy(nbody_batch *b);
+
+/* Admit a simulation: pos (n x 3), vel (n x 3, NULL = at rest), mass (n),
+ * host (on_device = 0; checked for non-finite values and negative masses,
+ * copied before the call returns) or device pointers (on_device = 1; read in
+ * stream order).  *slot receives its handle.  Errors: ENOSPC when no slot
+ * or no contiguous free range of n particles is left (retry after an
+ * eviction), EINVAL, ECUDA.  Does not synchronise. */
+int nbody_batch_admit(nbody_batch *b, int64_t n, int mode, double eps, double G, double dt,
+                      const double *pos, const double *vel, const double *mass, int on_device,
+                      int *slot);
+
+/* Remove a simulation and return its slot and range (stream-ordered). */
+int nbody_batch_evict(nbody_batch *b, int slot);
+
+/* Queue nticks ticks (each: one KDK step of every resident simulation). */
+int nbody_batch_step(nbody_batch *b, int64_t nticks);
+
+/* Wait for all queued work of the pool. */
+int nbody_batch_sync(nbody_batch *b);
+
+/* Non-blocking: 1 when all queued work of the pool has finished, 0 when some
+ * is still running, a negative code on error. */
+int nbody_batch_query(nbody_batch *b);
+
+/* State (n x 3 each; either may be NULL), time and step count of one
+ * simulation at its current step boundary.  Synchronises. */
+int nbody_batch_get_state(nbody_batch *b, int slot, double *pos, double *vel, double *t,
+                          int64_t *step, int on_device);
+
+/* a(t) and pot at the current positions of one simulation (after its first
+ * tick; ESTATE before).  Synchronises. */
+int nbody_batch_get_accel(nbody_batch *b, int slot, double *acc, double *pot, int on_device);
+
+/* Eq. 8-10 for one simulation (as nbody_diagnostics_ext).  Synchronises. */
+int nbody_batch_diagnostics(nbody_batch *b, int slot, double *E, double *K, double *W, double *P,
+                            double *L);
+
+/* Occupancy: resident simulations, particles in use (rounded to the pool
+ * alignment) and the largest free contiguous range. */
+int nbody_batch_info(nbody_batch *b, int *active, int64_t *used, int64_t *largest_free);
+int nbody_batch_slot_info(nbody_batch *b, int slot, int64_t *n, int *mode, int64_t *steps);
+
+/* Launch shape for one mode's force launches: i-particles per thread (1, 2,
+ * 4, 8) and target j-segment length (rounded up to the tile; a simulation
+ * is split into at most 16 segments).  Changes rounding order only. */
+int nbody_batch_set_launch(nbody_batch *b, int mode, int ipt, int64_t seg);
+
+/* FP64 force launches of this pool run as a persistent grid of at most
+ * blocks_per_sm thread blocks per SM (default 2; 0 = one block per work unit).
+ * FP64 work keeps the FP64 pipe busy with few warps; capping its residency
+ * leaves the rest of each SM to FP32-bound work of other streams (for
+ * instance a MIXED pool ticking at the same time). */
+int nbody_batch_set_fp64_residency(nbody_batch *b, int blocks_per_sm);
+
+/* Per-tick CUDA-event timing (see nbody_batch_profile_read). */
+int nbody_batch_profile(nbody_batch *b, int enable);
+
+/* Synchronise and return, for up to `cap` ticks recorded since the last
+ * read: tick_ms[k] (whole tick), force_ms[2k], force_ms[2k+1] (the FP64 and
+ * MIXED force launches, 0 when absent), inter[2k], inter[2k+1] (their
+ * interactions, n^2 summed over simulations); *nticks = ticks recorded.
+ * Any array may be NULL; the record is cleared. */
+int nbody_batch_profile_read(nbody_batch *b, int64_t cap, double *tick_ms, double *force_ms,
+                             double *inter, int64_t *nticks);
+
+/* Kernel launches issued by the pool since creation. */
+int64_t nbody_batch_launch_count(const nbody_batch *b);
+
 /*
  * Allocation-free variant of the binary64 force evaluation: the same Eq. 1-2
  * result as nbody_accel on an NBODY_FP64 context (acc n x 3, pot n, same

@@ -46,6 +46,27 @@ _SIGS = {
     "nbody_launch_count": (_i64, [_vp]),
     "nbody_profile": (_i, [_vp, _i]),
     "nbody_profile_read": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_i64)]),
+    "nbody_batch_bytes_per_particle": (_i64, []),
+    "nbody_batch_last_error": (ctypes.c_char_p, []),
+    "nbody_batch_create": (_i, [ctypes.POINTER(_vp), _i64, _i, _vp]),
+    "nbody_batch_destroy": (_i, [_vp]),
+    "nbody_batch_admit": (_i, [_vp, _i64, _i, _d, _d, _d, _vp, _vp, _vp, _i, ctypes.POINTER(_i)]),
+    "nbody_batch_evict": (_i, [_vp, _i]),
+    "nbody_batch_step": (_i, [_vp, _i64]),
+    "nbody_batch_sync": (_i, [_vp]),
+    "nbody_batch_query": (_i, [_vp]),
+    "nbody_batch_get_state": (_i, [_vp, _i, _vp, _vp, ctypes.POINTER(_d), ctypes.POINTER(_i64), _i]),
+    "nbody_batch_get_accel": (_i, [_vp, _i, _vp, _vp, _i]),
+    "nbody_batch_diagnostics": (_i, [_vp, _i, _dp, _dp, _dp, _dp, _dp]),
+    "nbody_batch_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "nbody_batch_slot_info": (_i, [_vp, _i, ctypes.POINTER(_i64), ctypes.POINTER(_i),
+                                   ctypes.POINTER(_i64)]),
+    "nbody_batch_set_launch": (_i, [_vp, _i, _i, _i64]),
+    "nbody_batch_profile": (_i, [_vp, _i]),
+    "nbody_batch_set_fp64_residency": (_i, [_vp, _i]),
+    "nbody_batch_profile_read": (_i, [_vp, _i64, _vp, _vp, _vp, ctypes.POINTER(_i64)]),
+    "nbody_batch_launch_count": (_i64, [_vp]),
+    "nbody_accel_f64_static": (_i, [_i64, _vp, _vp, _d, _d, _vp, _vp, _vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -57,7 +78,8 @@ for _name, (_res, _args) in _SIGS.items():
 class NbodyError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
-        detail = lib.nbody_last_error().decode(errors="replace")
+        getter = lib.nbody_batch_last_error if where.startswith("nbody_batch") else lib.nbody_last_error
+        detail = getter().decode(errors="replace")
         super().__init__(f"{where} failed ({code}): {detail}")
 
 

@@ -74,6 +74,40 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
   lo = __fadd_rn(lo, err);
 }
 
+// ---------------------------------------------------------------- work descriptors
+// A kernel runs units k = first(), first() + stride(), ... < count().
+// Dense: one system of n particles; block (x, y) = i-block x against j-segment y.
+struct DenseWork {
+  int64_t n, seg;
+  double eps2;
+  int per_block, tile;
+  __device__ __forceinline__ int64_t first() const { return 0; }
+  __device__ __forceinline__ int64_t stride() const { return 1; }
+  __device__ __forceinline__ int64_t count() const { return 1; }
+  __device__ __forceinline__ Unit get(int64_t) const {
+    Unit u;
+    u.i0 = (int64_t)blockIdx.x * per_block;
+    u.ni = (int)min((int64_t)per_block, n - u.i0);
+    u.j0 = (int64_t)blockIdx.y * seg;
+    u.nj = (int)min(seg, n - u.j0);
+    u.out = (int64_t)blockIdx.y * n + u.i0;
+    u.anchor = u.j0 / tile;
+    u.eps2 = eps2;
+    return u;
+  }
+};
+// Table: block x runs units[x], units[x + gridDim.x], ... (many systems of
+// uneven size in one launch; a grid smaller than the table makes the launch
+// persistent, which caps how many of its blocks sit on an SM at once).
+struct TableWork {
+  const Unit *units;
+  int64_t n;
+  __device__ __forceinline__ int64_t first() const { return blockIdx.x; }
+  __device__ __forceinline__ int64_t stride() const { return gridDim.x; }
+  __device__ __forceinline__ int64_t count() const { return n; }
+  __device__ __forceinline__ Unit get(int64_t k) const { return units[k]; }
+};
+
 // ---------------------------------------------------------------- binary64
 template <bool MASK>
 __device__ __forceinline__ void body_f64(const d4 &pj, double xi, double yi, double zi,
@@ -95,55 +129,55 @@ __device__ __forceinline__ void body_f64(const d4 &pj, double xi, double yi, dou
   pt += my;
 }
 
-template <int BT, int R, int T>
-__global__ void __launch_bounds__(BT) k_force_f64(const d4 *__restrict__ posm, int64_t n,
-                                                  double eps2, int64_t seg,
+template <int BT, int R, int T, class W>
+__global__ void __launch_bounds__(BT) k_force_f64(const d4 *__restrict__ posm, W work,
                                                   d4 *__restrict__ part) {
   __shared__ d4 tile[T];
-  const int tid = threadIdx.x;
-  const int64_t ib = (int64_t)blockIdx.x * (BT * R);
-  const int64_t j0 = (int64_t)blockIdx.y * seg;
-  const int64_t j1 = min(n, j0 + seg);
-  double xi[R], yi[R], zi[R], ax[R], ay[R], az[R], pt[R];
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    const int64_t i = ib + r * BT + tid;
-    const d4 p = posm[i < n ? i : n - 1];
-    xi[r] = p.x;
-    yi[r] = p.y;
-    zi[r] = p.z;
-    ax[r] = ay[r] = az[r] = pt[r] = 0.0;
-  }
-  for (int64_t jt = j0; jt < j1; jt += T) {
-    const int cnt = (int)min((int64_t)T, j1 - jt);
-    __syncthreads();
-    for (int k = tid; k < cnt; k += BT) tile[k] = posm[jt + k];
-    __syncthreads();
-    const bool diag = (jt < ib + BT * R) && (jt + cnt > ib);
-    if (cnt == T && !diag) {
-#pragma unroll 2
-      for (int k = 0; k < T; k++) {
-        const d4 pj = tile[k];
-#pragma unroll
-        for (int r = 0; r < R; r++)
-          body_f64<false>(pj, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pt[r], false);
-      }
-    } else {
-      for (int k = 0; k < cnt; k++) {
-        const d4 pj = tile[k];
-        const int64_t j = jt + k;
-#pragma unroll
-        for (int r = 0; r < R; r++)
-          body_f64<true>(pj, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pt[r],
-                         j == ib + r * BT + tid);
+  for (int64_t uk = work.first(); uk < work.count(); uk += work.stride()) {
+    const Unit u = work.get(uk);
+    const int tid = threadIdx.x;
+    const int64_t j1 = u.j0 + u.nj;
+    const double eps2 = u.eps2;
+    double xi[R], yi[R], zi[R], ax[R], ay[R], az[R], pt[R];
+  #pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int li = r * BT + tid;
+      const d4 p = posm[u.i0 + (li < u.ni ? li : 0)];
+      xi[r] = p.x;
+      yi[r] = p.y;
+      zi[r] = p.z;
+      ax[r] = ay[r] = az[r] = pt[r] = 0.0;
+    }
+    for (int64_t jt = u.j0; jt < j1; jt += T) {
+      const int cnt = (int)min((int64_t)T, j1 - jt);
+      __syncthreads();
+      for (int k = tid; k < cnt; k += BT) tile[k] = posm[jt + k];
+      __syncthreads();
+      const bool diag = (jt < u.i0 + u.ni) && (jt + cnt > u.i0);
+      if (cnt == T && !diag) {
+  #pragma unroll 2
+        for (int k = 0; k < T; k++) {
+          const d4 pj = tile[k];
+  #pragma unroll
+          for (int r = 0; r < R; r++)
+            body_f64<false>(pj, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pt[r], false);
+        }
+      } else {
+        for (int k = 0; k < cnt; k++) {
+          const d4 pj = tile[k];
+          const int64_t j = jt + k;
+  #pragma unroll
+          for (int r = 0; r < R; r++)
+            body_f64<true>(pj, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pt[r],
+                           j == u.i0 + r * BT + tid);
+        }
       }
     }
-  }
-  d4 *out = part + (int64_t)blockIdx.y * n;
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    const int64_t i = ib + r * BT + tid;
-    if (i < n) out[i] = d4{ax[r], ay[r], az[r], pt[r]};
+  #pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int li = r * BT + tid;
+      if (li < u.ni) part[u.out + li] = d4{ax[r], ay[r], az[r], pt[r]};
+    }
   }
 }
 
@@ -179,81 +213,80 @@ __device__ __forceinline__ void body_f32(const float4 &pj, float xi, float yi, f
 // ---------------------------------------------------------------- mixed
 // fpos[j] = (x_j - c_t, y_j - c_t, z_j - c_t, m_j) in binary32, c_t the anchor of
 // j's tile; anchor[2t] = float hi part of c_t, anchor[2t+1] = float lo part.
-template <int BT, int R, int T>
+template <int BT, int R, int T, class W>
 __global__ void __launch_bounds__(BT) k_force_mixed(const d4 *__restrict__ posm,
                                                     const float4 *__restrict__ fpos,
-                                                    const float4 *__restrict__ anchor, int64_t n,
-                                                    float eps2, int64_t seg,
+                                                    const float4 *__restrict__ anchor, W work,
                                                     d4 *__restrict__ part) {
   __shared__ float4 tile[T];
-  const int tid = threadIdx.x;
-  const int64_t ib = (int64_t)blockIdx.x * (BT * R);
-  const int64_t j0 = (int64_t)blockIdx.y * seg;
-  const int64_t j1 = min(n, j0 + seg);
-  float xh[R], yh[R], zh[R], xl[R], yl[R], zl[R];
-  float axh[R], axl[R], ayh[R], ayl[R], azh[R], azl[R], pth[R], ptl[R];
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    const int64_t i = ib + r * BT + tid;
-    const d4 p = posm[i < n ? i : n - 1];
-    xh[r] = __double2float_rn(p.x);
-    yh[r] = __double2float_rn(p.y);
-    zh[r] = __double2float_rn(p.z);
-    xl[r] = __double2float_rn(p.x - (double)xh[r]);
-    yl[r] = __double2float_rn(p.y - (double)yh[r]);
-    zl[r] = __double2float_rn(p.z - (double)zh[r]);
-    axh[r] = axl[r] = ayh[r] = ayl[r] = azh[r] = azl[r] = pth[r] = ptl[r] = 0.0f;
-  }
-  for (int64_t jt = j0; jt < j1; jt += T) {
-    const int cnt = (int)min((int64_t)T, j1 - jt);
-    __syncthreads();
-    for (int k = tid; k < cnt; k += BT) tile[k] = fpos[jt + k];
-    __syncthreads();
-    const int64_t tt = jt / T;
-    const float4 ch = anchor[2 * tt], cl = anchor[2 * tt + 1];
-    float xr[R], yr[R], zr[R], sx[R], sy[R], sz[R], sp[R];
-#pragma unroll
+  for (int64_t uk = work.first(); uk < work.count(); uk += work.stride()) {
+    const Unit u = work.get(uk);
+    const int tid = threadIdx.x;
+    const int64_t j1 = u.j0 + u.nj;
+    const float e2 = (float)u.eps2;
+    float xh[R], yh[R], zh[R], xl[R], yl[R], zl[R];
+    float axh[R], axl[R], ayh[R], ayl[R], azh[R], azl[R], pth[R], ptl[R];
+  #pragma unroll
     for (int r = 0; r < R; r++) {
-      xr[r] = __fadd_rn(__fsub_rn(xh[r], ch.x), __fsub_rn(xl[r], cl.x));
-      yr[r] = __fadd_rn(__fsub_rn(yh[r], ch.y), __fsub_rn(yl[r], cl.y));
-      zr[r] = __fadd_rn(__fsub_rn(zh[r], ch.z), __fsub_rn(zl[r], cl.z));
-      sx[r] = sy[r] = sz[r] = sp[r] = 0.0f;
+      const int li = r * BT + tid;
+      const d4 p = posm[u.i0 + (li < u.ni ? li : 0)];
+      xh[r] = __double2float_rn(p.x);
+      yh[r] = __double2float_rn(p.y);
+      zh[r] = __double2float_rn(p.z);
+      xl[r] = __double2float_rn(p.x - (double)xh[r]);
+      yl[r] = __double2float_rn(p.y - (double)yh[r]);
+      zl[r] = __double2float_rn(p.z - (double)zh[r]);
+      axh[r] = axl[r] = ayh[r] = ayl[r] = azh[r] = azl[r] = pth[r] = ptl[r] = 0.0f;
     }
-    const float e2 = eps2;
-    const bool diag = (jt < ib + BT * R) && (jt + cnt > ib);
-    if (cnt == T && !diag) {
-#pragma unroll 4
-      for (int k = 0; k < T; k++) {
-        const float4 pj = tile[k];
-#pragma unroll
-        for (int r = 0; r < R; r++)
-          body_f32<false, true>(pj, xr[r], yr[r], zr[r], e2, sx[r], sy[r], sz[r], sp[r], false);
+    for (int64_t jt = u.j0; jt < j1; jt += T) {
+      const int cnt = (int)min((int64_t)T, j1 - jt);
+      __syncthreads();
+      for (int k = tid; k < cnt; k += BT) tile[k] = fpos[jt + k];
+      __syncthreads();
+      const int64_t tt = u.anchor + (jt - u.j0) / T;
+      const float4 ch = anchor[2 * tt], cl = anchor[2 * tt + 1];
+      float xr[R], yr[R], zr[R], sx[R], sy[R], sz[R], sp[R];
+  #pragma unroll
+      for (int r = 0; r < R; r++) {
+        xr[r] = __fadd_rn(__fsub_rn(xh[r], ch.x), __fsub_rn(xl[r], cl.x));
+        yr[r] = __fadd_rn(__fsub_rn(yh[r], ch.y), __fsub_rn(yl[r], cl.y));
+        zr[r] = __fadd_rn(__fsub_rn(zh[r], ch.z), __fsub_rn(zl[r], cl.z));
+        sx[r] = sy[r] = sz[r] = sp[r] = 0.0f;
       }
-    } else {
-      for (int k = 0; k < cnt; k++) {
-        const float4 pj = tile[k];
-        const int64_t j = jt + k;
-#pragma unroll
-        for (int r = 0; r < R; r++)
-          body_f32<true, true>(pj, xr[r], yr[r], zr[r], e2, sx[r], sy[r], sz[r], sp[r],
-                         j == ib + r * BT + tid);
+      const bool diag = (jt < u.i0 + u.ni) && (jt + cnt > u.i0);
+      if (cnt == T && !diag) {
+  #pragma unroll 4
+        for (int k = 0; k < T; k++) {
+          const float4 pj = tile[k];
+  #pragma unroll
+          for (int r = 0; r < R; r++)
+            body_f32<false, true>(pj, xr[r], yr[r], zr[r], e2, sx[r], sy[r], sz[r], sp[r], false);
+        }
+      } else {
+        for (int k = 0; k < cnt; k++) {
+          const float4 pj = tile[k];
+          const int64_t j = jt + k;
+  #pragma unroll
+          for (int r = 0; r < R; r++)
+            body_f32<true, true>(pj, xr[r], yr[r], zr[r], e2, sx[r], sy[r], sz[r], sp[r],
+                                 j == u.i0 + r * BT + tid);
+        }
+      }
+  #pragma unroll
+      for (int r = 0; r < R; r++) {
+        two_sum_acc(axh[r], axl[r], sx[r]);
+        two_sum_acc(ayh[r], ayl[r], sy[r]);
+        two_sum_acc(azh[r], azl[r], sz[r]);
+        two_sum_acc(pth[r], ptl[r], sp[r]);
       }
     }
-#pragma unroll
+  #pragma unroll
     for (int r = 0; r < R; r++) {
-      two_sum_acc(axh[r], axl[r], sx[r]);
-      two_sum_acc(ayh[r], ayl[r], sy[r]);
-      two_sum_acc(azh[r], azl[r], sz[r]);
-      two_sum_acc(pth[r], ptl[r], sp[r]);
+      const int li = r * BT + tid;
+      if (li < u.ni)
+        part[u.out + li] = d4{(double)axh[r] + (double)axl[r], (double)ayh[r] + (double)ayl[r],
+                              (double)azh[r] + (double)azl[r], (double)pth[r] + (double)ptl[r]};
     }
-  }
-  d4 *out = part + (int64_t)blockIdx.y * n;
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    const int64_t i = ib + r * BT + tid;
-    if (i < n)
-      out[i] = d4{(double)axh[r] + (double)axl[r], (double)ayh[r] + (double)ayl[r],
-                  (double)azh[r] + (double)azl[r], (double)pth[r] + (double)ptl[r]};
   }
 }
 
@@ -265,15 +298,33 @@ __global__ void __launch_bounds__(BT) k_force_mixed(const d4 *__restrict__ posm,
 // sit far out in a halo (a bounding-box centre would be pulled out there and
 // cost every coordinate relative to it several digits).  It is found with a
 // bitonic sort of each coordinate in shared memory (tile = block = 256).
-template <int BT>
-__global__ void __launch_bounds__(BT) k_mixed_prep(const d4 *__restrict__ posm, int64_t n,
-                                                   int tile, float4 *__restrict__ fpos,
+struct DensePrep {
+  int64_t n;
+  int tile;
+  __device__ __forceinline__ PrepUnit get() const {
+    PrepUnit u;
+    u.anchor = blockIdx.x;
+    u.j0 = (int64_t)blockIdx.x * tile;
+    u.cnt = (int)min((int64_t)tile, n - u.j0);
+    u.pad = 0;
+    return u;
+  }
+};
+struct TablePrep {
+  const PrepUnit *units;
+  __device__ __forceinline__ PrepUnit get() const { return units[blockIdx.x]; }
+};
+
+template <int BT, class W>
+__global__ void __launch_bounds__(BT) k_mixed_prep(const d4 *__restrict__ posm, W work,
+                                                   float4 *__restrict__ fpos,
                                                    float4 *__restrict__ anchor) {
   static_assert((BT & (BT - 1)) == 0, "bitonic sort needs a power-of-two block");
   __shared__ double v[BT];
-  const int64_t t = blockIdx.x;
-  const int64_t j0 = t * tile;
-  const int cnt = (int)min((int64_t)tile, n - j0);
+  const PrepUnit pu = work.get();
+  const int64_t t = pu.anchor;
+  const int64_t j0 = pu.j0;
+  const int cnt = pu.cnt;
   const int tid = threadIdx.x;
   d4 p = {0, 0, 0, 0};
   if (tid < cnt) p = posm[j0 + tid];
@@ -312,55 +363,55 @@ __global__ void __launch_bounds__(BT) k_mixed_prep(const d4 *__restrict__ posm, 
 }
 
 // ---------------------------------------------------------------- binary32 (paper's SP)
-template <int BT, int R, int T>
-__global__ void __launch_bounds__(BT) k_force_f32(const float4 *__restrict__ posm, int64_t n,
-                                                  float eps2, int64_t seg,
+template <int BT, int R, int T, class W>
+__global__ void __launch_bounds__(BT) k_force_f32(const float4 *__restrict__ posm, W work,
                                                   float4 *__restrict__ part) {
   __shared__ float4 tile[T];
-  const int tid = threadIdx.x;
-  const int64_t ib = (int64_t)blockIdx.x * (BT * R);
-  const int64_t j0 = (int64_t)blockIdx.y * seg;
-  const int64_t j1 = min(n, j0 + seg);
-  float xi[R], yi[R], zi[R], ax[R], ay[R], az[R], pt[R];
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    const int64_t i = ib + r * BT + tid;
-    const float4 p = posm[i < n ? i : n - 1];
-    xi[r] = p.x;
-    yi[r] = p.y;
-    zi[r] = p.z;
-    ax[r] = ay[r] = az[r] = pt[r] = 0.0f;
-  }
-  for (int64_t jt = j0; jt < j1; jt += T) {
-    const int cnt = (int)min((int64_t)T, j1 - jt);
-    __syncthreads();
-    for (int k = tid; k < cnt; k += BT) tile[k] = posm[jt + k];
-    __syncthreads();
-    const bool diag = (jt < ib + BT * R) && (jt + cnt > ib);
-    if (cnt == T && !diag) {
-#pragma unroll 4
-      for (int k = 0; k < T; k++) {
-        const float4 pj = tile[k];
-#pragma unroll
-        for (int r = 0; r < R; r++)
-          body_f32<false, false>(pj, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pt[r], false);
-      }
-    } else {
-      for (int k = 0; k < cnt; k++) {
-        const float4 pj = tile[k];
-        const int64_t j = jt + k;
-#pragma unroll
-        for (int r = 0; r < R; r++)
-          body_f32<true, false>(pj, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pt[r],
-                         j == ib + r * BT + tid);
+  for (int64_t uk = work.first(); uk < work.count(); uk += work.stride()) {
+    const Unit u = work.get(uk);
+    const int tid = threadIdx.x;
+    const int64_t j1 = u.j0 + u.nj;
+    const float eps2 = (float)u.eps2;
+    float xi[R], yi[R], zi[R], ax[R], ay[R], az[R], pt[R];
+  #pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int li = r * BT + tid;
+      const float4 p = posm[u.i0 + (li < u.ni ? li : 0)];
+      xi[r] = p.x;
+      yi[r] = p.y;
+      zi[r] = p.z;
+      ax[r] = ay[r] = az[r] = pt[r] = 0.0f;
+    }
+    for (int64_t jt = u.j0; jt < j1; jt += T) {
+      const int cnt = (int)min((int64_t)T, j1 - jt);
+      __syncthreads();
+      for (int k = tid; k < cnt; k += BT) tile[k] = posm[jt + k];
+      __syncthreads();
+      const bool diag = (jt < u.i0 + u.ni) && (jt + cnt > u.i0);
+      if (cnt == T && !diag) {
+  #pragma unroll 4
+        for (int k = 0; k < T; k++) {
+          const float4 pj = tile[k];
+  #pragma unroll
+          for (int r = 0; r < R; r++)
+            body_f32<false, false>(pj, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pt[r], false);
+        }
+      } else {
+        for (int k = 0; k < cnt; k++) {
+          const float4 pj = tile[k];
+          const int64_t j = jt + k;
+  #pragma unroll
+          for (int r = 0; r < R; r++)
+            body_f32<true, false>(pj, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pt[r],
+                                  j == u.i0 + r * BT + tid);
+        }
       }
     }
-  }
-  float4 *out = part + (int64_t)blockIdx.y * n;
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    const int64_t i = ib + r * BT + tid;
-    if (i < n) out[i] = make_float4(ax[r], ay[r], az[r], pt[r]);
+  #pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int li = r * BT + tid;
+      if (li < u.ni) part[u.out + li] = make_float4(ax[r], ay[r], az[r], pt[r]);
+    }
   }
 }
 
@@ -368,6 +419,9 @@ __global__ void __launch_bounds__(BT) k_force_f32(const float4 *__restrict__ pos
 // Fixed block and tile sizes per arithmetic; R is chosen at run time.
 constexpr int BT_F64 = 128, T_F64 = 128;
 constexpr int BT_F32 = 256, T_F32 = 256;
+
+int force_block_threads(int mode) { return mode == NBODY_FP64 ? BT_F64 : BT_F32; }
+int force_tile(int mode) { return mode == NBODY_FP64 ? T_F64 : T_F32; }
 
 bool shape_supported(int mode, const Shape &sh) {
   if (sh.r != 1 && sh.r != 2 && sh.r != 4 && sh.r != 8) return false;
@@ -379,9 +433,9 @@ bool shape_supported(int mode, const Shape &sh) {
 template <int R>
 static const void *kernel_for(int mode) {
   switch (mode) {
-    case NBODY_FP64: return (const void *)k_force_f64<BT_F64, R, T_F64>;
-    case NBODY_MIXED: return (const void *)k_force_mixed<BT_F32, R, T_F32>;
-    default: return (const void *)k_force_f32<BT_F32, R, T_F32>;
+    case NBODY_FP64: return (const void *)k_force_f64<BT_F64, R, T_F64, DenseWork>;
+    case NBODY_MIXED: return (const void *)k_force_mixed<BT_F32, R, T_F32, DenseWork>;
+    default: return (const void *)k_force_f32<BT_F32, R, T_F32, DenseWork>;
   }
 }
 
@@ -402,18 +456,32 @@ int force_max_blocks_per_sm(int mode, const Shape &sh) {
   return nb;
 }
 
-template <int R>
-static void launch_r(int mode, const ForceIn &in, dim3 grid, cudaStream_t st) {
+template <int R, class W>
+static void launch_rw(int mode, const void *posm, const float4 *fpos, const float4 *anchor,
+                      const W &w, dim3 grid, void *part, cudaStream_t st) {
   if (mode == NBODY_FP64) {
-    k_force_f64<BT_F64, R, T_F64><<<grid, BT_F64, 0, st>>>(
-        (const d4 *)in.posm, in.n, in.eps2, in.seg, (d4 *)in.part);
+    k_force_f64<BT_F64, R, T_F64, W><<<grid, BT_F64, 0, st>>>((const d4 *)posm, w, (d4 *)part);
   } else if (mode == NBODY_MIXED) {
-    k_force_mixed<BT_F32, R, T_F32><<<grid, BT_F32, 0, st>>>(
-        (const d4 *)in.posm, in.fpos, in.anchor, in.n, (float)in.eps2, in.seg, (d4 *)in.part);
+    k_force_mixed<BT_F32, R, T_F32, W><<<grid, BT_F32, 0, st>>>((const d4 *)posm, fpos, anchor, w,
+                                                                (d4 *)part);
   } else {
-    k_force_f32<BT_F32, R, T_F32><<<grid, BT_F32, 0, st>>>(
-        (const float4 *)in.posm, in.n, (float)in.eps2, in.seg, (float4 *)in.part);
+    k_force_f32<BT_F32, R, T_F32, W><<<grid, BT_F32, 0, st>>>((const float4 *)posm, w,
+                                                              (float4 *)part);
   }
+}
+
+template <class W>
+static cudaError_t launch_w(int mode, int r, const void *posm, const float4 *fpos,
+                            const float4 *anchor, const W &w, dim3 grid, void *part,
+                            cudaStream_t st) {
+  switch (r) {
+    case 1: launch_rw<1>(mode, posm, fpos, anchor, w, grid, part, st); break;
+    case 2: launch_rw<2>(mode, posm, fpos, anchor, w, grid, part, st); break;
+    case 4: launch_rw<4>(mode, posm, fpos, anchor, w, grid, part, st); break;
+    case 8: launch_rw<8>(mode, posm, fpos, anchor, w, grid, part, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_force(int mode, const ForceIn &in, const Shape &sh, cudaStream_t st) {
@@ -421,21 +489,46 @@ cudaError_t launch_force(int mode, const ForceIn &in, const Shape &sh, cudaStrea
   const int64_t per_block = (int64_t)sh.bt * sh.r;
   const int64_t gx = (in.n + per_block - 1) / per_block;
   if (gx > 0x7fffffff) return cudaErrorInvalidValue;
-  const dim3 grid((unsigned)gx, (unsigned)sh.s);
-  switch (sh.r) {
-    case 1: launch_r<1>(mode, in, grid, st); break;
-    case 2: launch_r<2>(mode, in, grid, st); break;
-    case 4: launch_r<4>(mode, in, grid, st); break;
-    default: launch_r<8>(mode, in, grid, st); break;
-  }
-  return cudaGetLastError();
+  DenseWork w;
+  w.n = in.n;
+  w.seg = in.seg;
+  w.eps2 = in.eps2;
+  w.per_block = (int)per_block;
+  w.tile = sh.t;
+  return launch_w(mode, sh.r, in.posm, in.fpos, in.anchor, w, dim3((unsigned)gx, (unsigned)sh.s),
+                  in.part, st);
+}
+
+cudaError_t launch_force_units(int mode, const void *posm, const float4 *fpos,
+                               const float4 *anchor, const Unit *units, int64_t nunits, int r,
+                               void *part, int64_t max_blocks, cudaStream_t st) {
+  if (nunits < 1) return cudaErrorInvalidValue;
+  TableWork w;
+  w.units = units;
+  w.n = nunits;
+  int64_t g = nunits;
+  if (max_blocks > 0 && g > max_blocks) g = max_blocks;
+  if (g > 0x7fffffff) g = 0x7fffffff;
+  return launch_w(mode, r, posm, fpos, anchor, w, dim3((unsigned)g), part, st);
 }
 
 cudaError_t launch_mixed_prep(const d4 *posm, int64_t n, int tile, float4 *fpos, float4 *anchor,
                               cudaStream_t st) {
   if (tile != 256) return cudaErrorInvalidValue;  // one thread per tile member
   const int64_t nt = (n + tile - 1) / tile;
-  k_mixed_prep<256><<<(unsigned)nt, 256, 0, st>>>(posm, n, tile, fpos, anchor);
+  DensePrep w;
+  w.n = n;
+  w.tile = tile;
+  k_mixed_prep<256, DensePrep><<<(unsigned)nt, 256, 0, st>>>(posm, w, fpos, anchor);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_prep_units(const d4 *posm, const PrepUnit *units, int64_t nunits,
+                                    float4 *fpos, float4 *anchor, cudaStream_t st) {
+  if (nunits < 1 || nunits > 0x7fffffff) return cudaErrorInvalidValue;
+  TablePrep w;
+  w.units = units;
+  k_mixed_prep<256, TablePrep><<<(unsigned)nunits, 256, 0, st>>>(posm, w, fpos, anchor);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,22 @@ struct Shape {
   int s = 1;
 };
 
+// One thread block's share of a force evaluation: i-particles [i0, i0+ni)
+// against j-particles [j0, j0+nj) of the same system (pool indices), raw
+// partial sums written to part[out + (i - i0)].  anchor: MIXED tile-anchor
+// index of the tile that starts at j0.  eps2: that system's softening^2.
+struct Unit {
+  int64_t i0, j0, out, anchor;
+  double eps2;
+  int32_t ni, nj;
+};
+
+// One MIXED prep block: the tile [j0, j0+cnt) with anchor index `anchor`.
+struct PrepUnit {
+  int64_t j0, anchor;
+  int32_t cnt, pad;
+};
+
 // Raw force sums written by the force kernels, per j-segment s:
 //   part[s*n + i] = ( sum_j m_j (x_j - x_i) / w_ij, ..y.., ..z..,
 //                     sum_j m_j / sqrt(|d_ij|^2 + eps^2) )
@@ -63,6 +79,15 @@ struct ForceIn {
 
 // launchers (force.cu); return cudaError_t of the launch
 cudaError_t launch_force(int mode, const ForceIn &in, const Shape &sh, cudaStream_t st);
+// varlen: blocks run the units of `units` (device array), R i-particles per
+// thread; at most max_blocks blocks (0 = one per unit), each looping over units
+cudaError_t launch_force_units(int mode, const void *posm, const float4 *fpos,
+                               const float4 *anchor, const Unit *units, int64_t nunits, int r,
+                               void *part, int64_t max_blocks, cudaStream_t st);
+cudaError_t launch_mixed_prep_units(const d4 *posm, const PrepUnit *units, int64_t nunits,
+                                    float4 *fpos, float4 *anchor, cudaStream_t st);
+int force_block_threads(int mode);
+int force_tile(int mode);
 cudaError_t launch_mixed_prep(const d4 *posm, int64_t n, int tile, float4 *fpos, float4 *anchor,
                               cudaStream_t st);
 int force_max_blocks_per_sm(int mode, const Shape &sh);
