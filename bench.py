@@ -101,6 +101,18 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks(value, device="cpu"):
+    """Largest `value` over all ranks of the default process group (identity
+    without one): the slowest replica sets the whole job's time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -255,12 +267,7 @@ def run_gpu(args):
     mixed = time_mode(nb, torch, w, "mixed", args, flush)
 
     def agg(per_step):
-        ms = statistics.mean(per_step)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(statistics.mean(per_step), device="cuda")
 
     ms64 = agg(fp64["per_step"])
     msmx = agg(mixed["per_step"])
@@ -356,6 +363,19 @@ def run_gpu(args):
         torch.distributed.barrier()
 
 
+def profile_force(args):
+    """One force evaluation (Eq. 1-2) of the benchmark workload in one mode and
+    nothing else: the command the ncu captures of a single force launch run."""
+    import torch
+    import nbody_ics
+    import paper_1803_01190_gb300 as nb
+    w = nbody_ics.workload("disk_halo", n=args.n)
+    with nb.Simulation(args.n, mode=args.profile_force, eps=EPS) as sim:
+        sim.accel(w["pos"], w["mass"])
+        torch.cuda.synchronize()
+    print(json.dumps({"profile_force": args.profile_force, "n": args.n}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,10 +386,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--ref-rows", type=int, default=1024)
     ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--profile-force", choices=["fp64", "mixed", "fp32"], default=None,
+                    help="run one force evaluation of the workload in this mode and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.profile_force:
+        profile_force(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -24,12 +24,15 @@
 //         its seed from the binary32 special-function unit through integer
 //         bit moves (no FP64 conversion instruction) and refines it with one
 //         third-order step in binary64.
-//   mixed binary32 pair arithmetic on coordinates re-centred on an anchor (the
-//         per-coordinate median) per j-tile, with the i coordinates held as float-float pairs so that the
+//   mixed binary32 pair arithmetic (packed: two j per instruction, SFU
+//         reciprocal square root plus one Newton step) on coordinates
+//         re-centred on an anchor (the per-coordinate median) per j-tile, with the i coordinates held as float-float pairs so that the
 //         per-tile shift costs three binary32 operations per coordinate and no
 //         FP64 instruction; per-tile binary32 partial sums are folded into
 //         float-float (compensated, TwoSum) accumulators, returned as binary64.
-//   f32   binary32 throughout with plain binary32 accumulation: the paper's SP.
+//   f32   binary32 throughout (packed pairs, SFU reciprocal square root) with
+//         plain binary32 accumulation: the paper's SP.  The two halves of a
+//         thread's packed accumulators (even and odd j) are added at the end.
 #include <cuda_runtime.h>
 
 #include "nbody_internal.cuh"
@@ -181,33 +184,57 @@ __global__ void __launch_bounds__(BT) k_force_f64(const d4 *__restrict__ posm, W
   }
 }
 
-// ---------------------------------------------------------------- binary32 pair body
-// REFINE: one Newton step y = y0 + y0 (1 - r2 y0^2) / 2 on the SFU result.  The
-// SFU approximation's error has a systematic part that adds up coherently
-// over the N terms of a sum; the Newton step (4 more binary32 instructions)
-// leaves an error of about one rounding, which averages out instead.
+// ---------------------------------------------------------------- packed binary32 pairs
+// Two j-particles per instruction with the packed FP32 instructions of sm_100+
+// (one issue slot drives two lanes of FMA-pipe work).  Shared-memory tile
+// entry k holds j = 2k and 2k+1 as A = (x0, x1, y0, y1), B = (z0, z1, m0, m1).
+// (nx, ny, nz) are the negated i coordinates in both halves.  An odd tail is
+// padded with a massless particle at 1e18 (finite r^2, zero contribution).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
 template <bool MASK, bool REFINE>
-__device__ __forceinline__ void body_f32(const float4 &pj, float xi, float yi, float zi,
-                                         float eps2, float &ax, float &ay, float &az, float &pt,
-                                         bool self) {
-  const float dx = pj.x - xi, dy = pj.y - yi, dz = pj.z - zi;
-  float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-  float m = pj.w;
-  if (MASK && self) {
-    r2 = 1.0f;
-    m = 0.0f;
+__device__ __forceinline__ void body_pair(const float4 &A, const float4 &B, float2 nx, float2 ny,
+                                          float2 nz, float2 e2, float2 &ax, float2 &ay,
+                                          float2 &az, float2 &pt, bool self0, bool self1) {
+  const float2 dx = __fadd2_rn(f2(A.x, A.y), nx);
+  const float2 dy = __fadd2_rn(f2(A.z, A.w), ny);
+  const float2 dz = __fadd2_rn(f2(B.x, B.y), nz);
+  float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+  float2 m = f2(B.z, B.w);
+  if (MASK) {
+    if (self0) {
+      r2.x = 1.0f;
+      m.x = 0.0f;
+    }
+    if (self1) {
+      r2.y = 1.0f;
+      m.y = 0.0f;
+    }
   }
-  float y = rsqrt_approx(r2);
-  if (REFINE) {
-    const float e = fmaf(-(r2 * y), y, 1.0f);
-    y = fmaf(y * 0.5f, e, y);
+  float2 y = f2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+  if (REFINE) {  // y += y (1 - r2 y^2) / 2, as (-y/2) (r2 y^2 - 1) + y
+    const float2 e = __ffma2_rn(__fmul2_rn(r2, y), y, f2(-1.0f, -1.0f));
+    y = __ffma2_rn(__fmul2_rn(y, f2(-0.5f, -0.5f)), e, y);
   }
-  const float my = m * y;
-  const float f = my * (y * y);
-  ax = fmaf(dx, f, ax);
-  ay = fmaf(dy, f, ay);
-  az = fmaf(dz, f, az);
-  pt += my;
+  const float2 my = __fmul2_rn(m, y);
+  const float2 f = __fmul2_rn(my, __fmul2_rn(y, y));
+  ax = __ffma2_rn(dx, f, ax);
+  ay = __ffma2_rn(dy, f, ay);
+  az = __ffma2_rn(dz, f, az);
+  pt = __fadd2_rn(pt, my);
+}
+
+// Stage j-particles [jt, jt+cnt) of `src` (float4 x, y, z, m) as pairs.
+template <int BT, int T>
+__device__ __forceinline__ void load_pairs(const float4 *__restrict__ src, int64_t jt, int cnt,
+                                           float4 *tA, float4 *tB) {
+  const float4 dummy = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  for (int k = threadIdx.x; 2 * k < cnt; k += BT) {
+    const float4 a = src[jt + 2 * k];
+    const float4 b = 2 * k + 1 < cnt ? src[jt + 2 * k + 1] : dummy;
+    tA[k] = make_float4(a.x, b.x, a.y, b.y);
+    tB[k] = make_float4(a.z, b.z, a.w, b.w);
+  }
 }
 
 // ---------------------------------------------------------------- mixed
@@ -218,15 +245,15 @@ __global__ void __launch_bounds__(BT) k_force_mixed(const d4 *__restrict__ posm,
                                                     const float4 *__restrict__ fpos,
                                                     const float4 *__restrict__ anchor, W work,
                                                     d4 *__restrict__ part) {
-  __shared__ float4 tile[T];
+  __shared__ float4 tA[T / 2], tB[T / 2];
   for (int64_t uk = work.first(); uk < work.count(); uk += work.stride()) {
     const Unit u = work.get(uk);
     const int tid = threadIdx.x;
     const int64_t j1 = u.j0 + u.nj;
-    const float e2 = (float)u.eps2;
+    const float2 e2 = f2((float)u.eps2, (float)u.eps2);
     float xh[R], yh[R], zh[R], xl[R], yl[R], zl[R];
     float axh[R], axl[R], ayh[R], ayl[R], azh[R], azl[R], pth[R], ptl[R];
-  #pragma unroll
+#pragma unroll
     for (int r = 0; r < R; r++) {
       const int li = r * BT + tid;
       const d4 p = posm[u.i0 + (li < u.ni ? li : 0)];
@@ -241,46 +268,53 @@ __global__ void __launch_bounds__(BT) k_force_mixed(const d4 *__restrict__ posm,
     for (int64_t jt = u.j0; jt < j1; jt += T) {
       const int cnt = (int)min((int64_t)T, j1 - jt);
       __syncthreads();
-      for (int k = tid; k < cnt; k += BT) tile[k] = fpos[jt + k];
+      load_pairs<BT, T>(fpos, jt, cnt, tA, tB);
       __syncthreads();
       const int64_t tt = u.anchor + (jt - u.j0) / T;
       const float4 ch = anchor[2 * tt], cl = anchor[2 * tt + 1];
-      float xr[R], yr[R], zr[R], sx[R], sy[R], sz[R], sp[R];
-  #pragma unroll
+      float2 nx[R], ny[R], nz[R], sx[R], sy[R], sz[R], sp[R];
+#pragma unroll
       for (int r = 0; r < R; r++) {
-        xr[r] = __fadd_rn(__fsub_rn(xh[r], ch.x), __fsub_rn(xl[r], cl.x));
-        yr[r] = __fadd_rn(__fsub_rn(yh[r], ch.y), __fsub_rn(yl[r], cl.y));
-        zr[r] = __fadd_rn(__fsub_rn(zh[r], ch.z), __fsub_rn(zl[r], cl.z));
-        sx[r] = sy[r] = sz[r] = sp[r] = 0.0f;
+        const float x = __fadd_rn(__fsub_rn(xh[r], ch.x), __fsub_rn(xl[r], cl.x));
+        const float y = __fadd_rn(__fsub_rn(yh[r], ch.y), __fsub_rn(yl[r], cl.y));
+        const float z = __fadd_rn(__fsub_rn(zh[r], ch.z), __fsub_rn(zl[r], cl.z));
+        nx[r] = f2(-x, -x);
+        ny[r] = f2(-y, -y);
+        nz[r] = f2(-z, -z);
+        sx[r] = sy[r] = sz[r] = sp[r] = f2(0.0f, 0.0f);
       }
+      const int np = (cnt + 1) / 2;
       const bool diag = (jt < u.i0 + u.ni) && (jt + cnt > u.i0);
       if (cnt == T && !diag) {
-  #pragma unroll 4
-        for (int k = 0; k < T; k++) {
-          const float4 pj = tile[k];
-  #pragma unroll
+#pragma unroll 2
+        for (int k = 0; k < T / 2; k++) {
+          const float4 A = tA[k], B = tB[k];
+#pragma unroll
           for (int r = 0; r < R; r++)
-            body_f32<false, true>(pj, xr[r], yr[r], zr[r], e2, sx[r], sy[r], sz[r], sp[r], false);
+            body_pair<false, true>(A, B, nx[r], ny[r], nz[r], e2, sx[r], sy[r], sz[r], sp[r],
+                                   false, false);
         }
       } else {
-        for (int k = 0; k < cnt; k++) {
-          const float4 pj = tile[k];
-          const int64_t j = jt + k;
-  #pragma unroll
-          for (int r = 0; r < R; r++)
-            body_f32<true, true>(pj, xr[r], yr[r], zr[r], e2, sx[r], sy[r], sz[r], sp[r],
-                                 j == u.i0 + r * BT + tid);
+        for (int k = 0; k < np; k++) {
+          const float4 A = tA[k], B = tB[k];
+          const int64_t j = jt + 2 * k;
+#pragma unroll
+          for (int r = 0; r < R; r++) {
+            const int64_t i = u.i0 + r * BT + tid;
+            body_pair<true, true>(A, B, nx[r], ny[r], nz[r], e2, sx[r], sy[r], sz[r], sp[r],
+                                  j == i, j + 1 == i);
+          }
         }
       }
-  #pragma unroll
+#pragma unroll
       for (int r = 0; r < R; r++) {
-        two_sum_acc(axh[r], axl[r], sx[r]);
-        two_sum_acc(ayh[r], ayl[r], sy[r]);
-        two_sum_acc(azh[r], azl[r], sz[r]);
-        two_sum_acc(pth[r], ptl[r], sp[r]);
+        two_sum_acc(axh[r], axl[r], __fadd_rn(sx[r].x, sx[r].y));
+        two_sum_acc(ayh[r], ayl[r], __fadd_rn(sy[r].x, sy[r].y));
+        two_sum_acc(azh[r], azl[r], __fadd_rn(sz[r].x, sz[r].y));
+        two_sum_acc(pth[r], ptl[r], __fadd_rn(sp[r].x, sp[r].y));
       }
     }
-  #pragma unroll
+#pragma unroll
     for (int r = 0; r < R; r++) {
       const int li = r * BT + tid;
       if (li < u.ni)
@@ -366,51 +400,57 @@ __global__ void __launch_bounds__(BT) k_mixed_prep(const d4 *__restrict__ posm, 
 template <int BT, int R, int T, class W>
 __global__ void __launch_bounds__(BT) k_force_f32(const float4 *__restrict__ posm, W work,
                                                   float4 *__restrict__ part) {
-  __shared__ float4 tile[T];
+  __shared__ float4 tA[T / 2], tB[T / 2];
   for (int64_t uk = work.first(); uk < work.count(); uk += work.stride()) {
     const Unit u = work.get(uk);
     const int tid = threadIdx.x;
     const int64_t j1 = u.j0 + u.nj;
-    const float eps2 = (float)u.eps2;
-    float xi[R], yi[R], zi[R], ax[R], ay[R], az[R], pt[R];
-  #pragma unroll
+    const float2 e2 = f2((float)u.eps2, (float)u.eps2);
+    float2 nx[R], ny[R], nz[R], ax[R], ay[R], az[R], pt[R];
+#pragma unroll
     for (int r = 0; r < R; r++) {
       const int li = r * BT + tid;
       const float4 p = posm[u.i0 + (li < u.ni ? li : 0)];
-      xi[r] = p.x;
-      yi[r] = p.y;
-      zi[r] = p.z;
-      ax[r] = ay[r] = az[r] = pt[r] = 0.0f;
+      nx[r] = f2(-p.x, -p.x);
+      ny[r] = f2(-p.y, -p.y);
+      nz[r] = f2(-p.z, -p.z);
+      ax[r] = ay[r] = az[r] = pt[r] = f2(0.0f, 0.0f);
     }
     for (int64_t jt = u.j0; jt < j1; jt += T) {
       const int cnt = (int)min((int64_t)T, j1 - jt);
       __syncthreads();
-      for (int k = tid; k < cnt; k += BT) tile[k] = posm[jt + k];
+      load_pairs<BT, T>(posm, jt, cnt, tA, tB);
       __syncthreads();
+      const int np = (cnt + 1) / 2;
       const bool diag = (jt < u.i0 + u.ni) && (jt + cnt > u.i0);
       if (cnt == T && !diag) {
-  #pragma unroll 4
-        for (int k = 0; k < T; k++) {
-          const float4 pj = tile[k];
-  #pragma unroll
+#pragma unroll 2
+        for (int k = 0; k < T / 2; k++) {
+          const float4 A = tA[k], B = tB[k];
+#pragma unroll
           for (int r = 0; r < R; r++)
-            body_f32<false, false>(pj, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pt[r], false);
+            body_pair<false, false>(A, B, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], pt[r],
+                                    false, false);
         }
       } else {
-        for (int k = 0; k < cnt; k++) {
-          const float4 pj = tile[k];
-          const int64_t j = jt + k;
-  #pragma unroll
-          for (int r = 0; r < R; r++)
-            body_f32<true, false>(pj, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pt[r],
-                                  j == u.i0 + r * BT + tid);
+        for (int k = 0; k < np; k++) {
+          const float4 A = tA[k], B = tB[k];
+          const int64_t j = jt + 2 * k;
+#pragma unroll
+          for (int r = 0; r < R; r++) {
+            const int64_t i = u.i0 + r * BT + tid;
+            body_pair<true, false>(A, B, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], pt[r],
+                                   j == i, j + 1 == i);
+          }
         }
       }
     }
-  #pragma unroll
+#pragma unroll
     for (int r = 0; r < R; r++) {
       const int li = r * BT + tid;
-      if (li < u.ni) part[u.out + li] = make_float4(ax[r], ay[r], az[r], pt[r]);
+      if (li < u.ni)
+        part[u.out + li] = make_float4(__fadd_rn(ax[r].x, ax[r].y), __fadd_rn(ay[r].x, ay[r].y),
+                                       __fadd_rn(az[r].x, az[r].y), __fadd_rn(pt[r].x, pt[r].y));
     }
   }
 }

@@ -9,11 +9,11 @@ the next tick.  All arithmetic runs in the library's CUDA kernels; this
 module only schedules.
 
 Autotuner: the launch shape of each mode's force launch (i-particles per
-thread, j-segment length) is chosen per load bucket (the mode and log2 of
-the interactions in the tick) from the force-kernel time per interaction
-measured with CUDA events on the ticks themselves: every candidate is tried
-a few times per bucket, then the fastest is used, with an occasional
-re-check.  A shape changes rounding order only.
+thread, j-segment length) is chosen per load bucket (the mode and the
+tick's interactions to within a factor of 8) from the force-kernel time per
+interaction measured with CUDA events on the ticks themselves: every
+candidate is tried once per bucket, then the fastest is used, with a
+periodic re-check of the runner-up.  A shape changes rounding order only.
 """
 import collections
 import ctypes
@@ -159,8 +159,8 @@ class Batch:
 class Autotuner:
     """Chooses (ipt, seg) per (mode, load bucket) from measured ns per interaction."""
 
-    def __init__(self, candidates=None, trials=2, recheck_every=64):
-        self.candidates = candidates or [(ipt, seg) for ipt in (1, 2, 4) for seg in (2048, 8192, 32768)]
+    def __init__(self, candidates=None, trials=1, recheck_every=64):
+        self.candidates = candidates or [(ipt, seg) for ipt in (2, 1, 4) for seg in (8192, 2048)]
         self.trials = trials
         self.recheck_every = recheck_every
         self.stats = collections.defaultdict(lambda: collections.defaultdict(list))
@@ -168,7 +168,8 @@ class Autotuner:
 
     @staticmethod
     def bucket(mode, interactions):
-        return (mode, int(math.log2(max(interactions, 1.0))))
+        """Load bucket: the mode and the tick's interactions to within a factor of 8."""
+        return (mode, int(math.log2(max(interactions, 1.0)) // 3))
 
     def choose(self, key):
         st = self.stats[key]

@@ -16,6 +16,7 @@ def test_autotuner_explores_then_exploits(serve):
     t = serve.Autotuner(candidates=[(1, 1), (2, 1), (4, 1)], trials=2, recheck_every=5)
     cost = {(1, 1): 3.0, (2, 1): 1.0, (4, 1): 2.0}
     key = serve.Autotuner.bucket("fp64", 1e9)
+    assert serve.Autotuner.bucket("fp64", 1.5e9) == key           # within a factor of 8
     seen = []
     for _ in range(6):                     # exploration: each candidate twice
         c = t.choose(key)
