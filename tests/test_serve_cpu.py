@@ -15,8 +15,8 @@ def serve():
 def test_autotuner_explores_then_exploits(serve):
     t = serve.Autotuner(candidates=[(1, 1), (2, 1), (4, 1)], trials=2, recheck_every=5)
     cost = {(1, 1): 3.0, (2, 1): 1.0, (4, 1): 2.0}
-    key = serve.Autotuner.bucket("fp64", 1e9)
-    assert serve.Autotuner.bucket("fp64", 1.5e9) == key           # within a factor of 8
+    key = serve.Autotuner.bucket("fp64", 2.0 ** 31)
+    assert serve.Autotuner.bucket("fp64", 2.0 ** 32) == key       # same factor-of-8 bucket
     seen = []
     for _ in range(6):                     # exploration: each candidate twice
         c = t.choose(key)
@@ -32,7 +32,7 @@ def test_autotuner_explores_then_exploits(serve):
     assert t.best(key) == (2, 1)
     # buckets are separate: another load starts exploring again
     assert t.choose(serve.Autotuner.bucket("fp64", 1e12)) == (1, 1)
-    assert serve.Autotuner.bucket("mixed", 1e9) != key
+    assert serve.Autotuner.bucket("mixed", 2.0 ** 31) != key
 
 
 def test_autotuner_follows_a_change(serve):
