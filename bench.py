@@ -265,12 +265,14 @@ def run_gpu(args):
 
     fp64 = time_mode(nb, torch, w, "fp64", args, flush, clocks=clocks)
     mixed = time_mode(nb, torch, w, "mixed", args, flush)
+    f64e = time_mode(nb, torch, w, "f64e", args, flush)
 
     def agg(per_step):
         return max_over_ranks(statistics.mean(per_step), device="cuda")
 
     ms64 = agg(fp64["per_step"])
     msmx = agg(mixed["per_step"])
+    msfe = agg(f64e["per_step"])
     value = world * inter / (ms64 * 1e-3) / 1e9
     value_mx = world * inter / (msmx * 1e-3) / 1e9
 
@@ -297,6 +299,9 @@ def run_gpu(args):
     ao64, po64, smag = oracle.accel(p64, w["mass"], EPS, 1.0, rows=rows, threads=cores)
     cpu_s = time.perf_counter() - t0
     aomx, _, _ = oracle.accel(pmx, w["mass"], EPS, 1.0, rows=rows, threads=cores)
+    pfe, _, _, _ = f64e["sim"].get_state()
+    afe, _ = f64e["sim"].get_accel()
+    aofe, _, smag_fe = oracle.accel(pfe, w["mass"], EPS, 1.0, rows=rows, threads=cores)
     cpu_value = len(rows) * n / cpu_s / 1e9
 
     def errs(a, ao):
@@ -340,7 +345,20 @@ def run_gpu(args):
                          "sample": f"{len(rows)} sampled i-particles x all {n} j of the FP64 "
                                    f"state after the timed steps ({cpu_s:.1f} s)"},
         "force_error_vs_oracle": {"fp64": {**errs(a64, ao64), "gate_1e-12_pass": bool(gate.all())},
+                                  "f64e": {**errs(afe, aofe), "gate_1e-12_pass_fraction": float(np.mean(
+                                      np.linalg.norm(afe[rows] - aofe, axis=1) <= 1e-12 * np.linalg.norm(aofe, axis=1)
+                                      + 4 * U * np.sqrt(n) * smag_fe))},
                                   "mixed": errs(amx, aomx), "rows": len(rows)},
+        "f64e": {"value": world * inter / (msfe * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": msfe,
+                 "speedup_vs_fp64": (world * inter / (msfe * 1e-3) / 1e9) / value,
+                 "force_ms_per_launch": f64e["force_ms"],
+                 "note": "binary64-class float-float arithmetic on the FP32 pipes (about 48 bits)",
+                 "roofline": {"bound": "alu", "kernel": "k_force_f64e",
+                              "achieved": inter * FLOP_PER_INTERACTION / (f64e["force_ms"] * 1e-3) / 1e12,
+                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": inter * FLOP_PER_INTERACTION / (f64e["force_ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                              "peak_source": "the FP64 peak it replaces (derived, 1.259 TFLOP/s)"},
+                 "gpu_launches": f64e["launches"] * world, "launch": f64e["sim"].get_launch()},
         "mixed": {"value": value_mx, "unit": UNIT, "ms_per_step": msmx,
                   "speedup_vs_fp64": value_mx / value,
                   "p50_step_ms": float(np.percentile(mixed["per_step"], 50)),
@@ -355,6 +373,7 @@ def run_gpu(args):
                   "gpu_launches": mixed["launches"] * world,
                   "launch": mixed["sim"].get_launch()},
         "drift_over_timed_steps": {"fp64": drift(fp64["diag0"], fp64["diags"]),
+                                   "f64e": drift(f64e["diag0"], f64e["diags"]),
                                    "mixed": drift(mixed["diag0"], mixed["diags"])},
         "serving": serving,
     }
@@ -386,7 +405,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--ref-rows", type=int, default=1024)
     ap.add_argument("--serve-seconds", type=float, default=30.0)
-    ap.add_argument("--profile-force", choices=["fp64", "mixed", "fp32"], default=None,
+    ap.add_argument("--profile-force", choices=["fp64", "f64e", "mixed", "fp32"], default=None,
                     help="run one force evaluation of the workload in this mode and exit")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -51,6 +51,10 @@ extern "C" {
                           binary64 storage; tile partial sums accumulated with compensation
                           and returned in binary64; state and update in binary64 */
 #define NBODY_FP32  2  /* binary32 throughout, state included: the paper's single precision (SP) */
+#define NBODY_F64E  3  /* binary64-class accuracy from float-float (about 48-bit) arithmetic on
+                          the binary32 pipes, on coordinates re-centred per j-tile; tile partial
+                          sums folded into binary64; state and update in binary64.  Not offered
+                          by the batch interface. */
 
 /* ---- time integration schemes ------------------------------------------ */
 #define NBODY_KDK 0    /* Eq. 5-7 (section 1): predictor, drift, one force evaluation, corrector */

@@ -18,10 +18,10 @@ import os
 import numpy as np
 
 from . import _abi
-from ._abi import (FP32, FP64, KDK, MIXED, RK4, NbodyError, check, lib,  # noqa: F401
+from ._abi import (F64E, FP32, FP64, KDK, MIXED, RK4, NbodyError, check, lib,  # noqa: F401
                    library_path)
 
-MODES = {"fp64": FP64, "mixed": MIXED, "fp32": FP32}
+MODES = {"fp64": FP64, "mixed": MIXED, "fp32": FP32, "f64e": F64E}
 SCHEMES = {"kdk": KDK, "rk4": RK4}
 
 __all__ = ["Simulation", "NbodyError", "MODES", "SCHEMES", "lib", "library_path", "build"]
@@ -72,7 +72,7 @@ def _current_stream():
 class Simulation:
     """One N-body system resident on the GPU (a context of the C ABI).
 
-    mode: "fp64" | "mixed" | "fp32"; eps: softening (the paper's delta);
+    mode: "fp64" | "f64e" | "mixed" | "fp32"; eps: softening (the paper's delta);
     G: gravitational constant; stream: a torch.cuda.Stream (default: the
     current one at creation)."""
 

@@ -17,7 +17,7 @@ if not os.path.exists(library_path):
 lib = ctypes.CDLL(library_path)
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, ENOSPC = 0, -1, -2, -3, -4, -5, -6
-FP64, MIXED, FP32 = 0, 1, 2
+FP64, MIXED, FP32, F64E = 0, 1, 2, 3
 KDK, RK4 = 0, 1
 
 _vp = ctypes.c_void_p

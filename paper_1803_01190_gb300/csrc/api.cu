@@ -91,14 +91,12 @@ static int sync(nbody_ctx *c) {
 // Default launch shape: enough thread blocks to fill every SM several times.
 static void default_shape(nbody_ctx *c, nb::Shape &sh, int r_req, int s_req) {
   sh = nb::Shape();
-  if (c->mode == NBODY_FP64) {
-    sh.bt = 128;
-    sh.t = 128;
-  } else {
-    sh.bt = 256;
-    sh.t = 256;
-  }
-  int r = r_req ? r_req : 4;
+  sh.bt = nb::force_block_threads(c->mode);
+  sh.t = nb::force_tile(c->mode);
+  // measured on GB300: FP64 is FP64-pipe bound at any R; the packed FP32 and
+  // float-float kernels keep enough warps resident only at R = 2
+  int r = r_req ? r_req : (c->mode == NBODY_FP64 ? 4 : 2);
+  if (c->mode == NBODY_F64E && r > 4) r = 4;
   while (!r_req && r > 1 && (int64_t)sh.bt * r * c->num_sms > c->n) r >>= 1;
   sh.r = r;
   const int64_t bx = (c->n + (int64_t)sh.bt * r - 1) / ((int64_t)sh.bt * r);
@@ -141,8 +139,9 @@ static int force(nbody_ctx *c, const void *posm_in, int &S) {
   const int64_t seg = seg_len(c, S);
   int rc = ensure_part(c, S);
   if (rc) return rc;
-  if (c->mode == NBODY_MIXED) {
-    CK(nb::launch_mixed_prep((const d4 *)posm_in, c->n, c->shape.t, c->fpos, c->anchor, c->st));
+  if (c->mode == NBODY_MIXED || c->mode == NBODY_F64E) {
+    CK(nb::launch_mixed_prep((const d4 *)posm_in, c->n, c->shape.t, c->fpos, c->anchor, c->st,
+                             c->mode == NBODY_F64E));
     c->launches++;
   }
   nb::ForceIn in;
@@ -238,7 +237,7 @@ int nbody_create(nbody_ctx **out, int64_t n, int mode, double eps, double G, voi
   if (!out) return fail(NBODY_EINVAL, "out is NULL");
   *out = nullptr;
   if (n < 1) return fail(NBODY_EINVAL, "n < 1");
-  if (mode != NBODY_FP64 && mode != NBODY_MIXED && mode != NBODY_FP32)
+  if (mode != NBODY_FP64 && mode != NBODY_MIXED && mode != NBODY_FP32 && mode != NBODY_F64E)
     return fail(NBODY_EINVAL, "unknown mode");
   if (!(eps >= 0) || !std::isfinite(eps)) return fail(NBODY_EINVAL, "eps must be finite and >= 0");
   if (!std::isfinite(G)) return fail(NBODY_EINVAL, "G must be finite");
@@ -265,9 +264,10 @@ int nbody_create(nbody_ctx **out, int64_t n, int mode, double eps, double G, voi
             cudaMalloc(&c->diag_out, 16 * sizeof(double)) == cudaSuccess &&
             cudaMallocHost(&c->h_diag, 16 * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->diag_blocks, (size_t)nb::diag_blocks(n) * 8 * sizeof(double)) == cudaSuccess;
-  if (ok && mode == NBODY_MIXED) {
+  if (ok && (mode == NBODY_MIXED || mode == NBODY_F64E)) {
     const int64_t tiles = (n + 255) / 256;
-    ok = cudaMalloc(&c->fpos, (size_t)n * sizeof(float4)) == cudaSuccess &&
+    const size_t per = mode == NBODY_F64E ? 2 : 1;  // float4 per particle
+    ok = cudaMalloc(&c->fpos, (size_t)n * per * sizeof(float4)) == cudaSuccess &&
          cudaMalloc(&c->anchor, (size_t)tiles * 2 * sizeof(float4)) == cudaSuccess;
   }
   if (!ok) {

@@ -30,10 +30,17 @@
 //         per-tile shift costs three binary32 operations per coordinate and no
 //         FP64 instruction; per-tile binary32 partial sums are folded into
 //         float-float (compensated, TwoSum) accumulators, returned as binary64.
+//   f64e  binary64-class accuracy on the binary32 pipes: float-float (about 48
+//         significant bits) pair arithmetic on coordinates re-centred per
+//         j-tile, float-float tile partials folded into binary64 per tile.
+//         About 160 binary32 instructions per pair, but on pipes 64 times
+//         faster than GB300's FP64 pipe.
 //   f32   binary32 throughout (packed pairs, SFU reciprocal square root) with
 //         plain binary32 accumulation: the paper's SP.  The two halves of a
 //         thread's packed accumulators (even and odd j) are added at the end.
 #include <cuda_runtime.h>
+
+#include <cstring>
 
 #include "nbody_internal.cuh"
 
@@ -237,6 +244,249 @@ __device__ __forceinline__ void load_pairs(const float4 *__restrict__ src, int64
   }
 }
 
+// ---------------------------------------------------------------- float-float (F64E)
+// Binary64-class arithmetic on the binary32 pipes: every quantity is an
+// unevaluated sum hi + lo of two floats (about 48 significant bits), built
+// from the error-free transformations TwoSum (Knuth), Fast2Sum (Dekker,
+// |a| >= |b|) and TwoProd via FMA; two j-particles per packed instruction.
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+  unsigned long long A, B, D;
+  memcpy(&A, &a, 8);
+  memcpy(&B, &b, 8);
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(D) : "l"(A), "l"(B));
+  float2 d;
+  memcpy(&d, &D, 8);
+  return d;
+}
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+  s = __fadd2_rn(a, b);
+  const float2 bb = fsub2(s, a);
+  e = __fadd2_rn(fsub2(a, fsub2(s, bb)), fsub2(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+  s = __fadd2_rn(a, b);
+  e = fsub2(b, fsub2(s, a));
+}
+__device__ __forceinline__ void two_prod2(float2 a, float2 b, float2 &p, float2 &e) {
+  p = __fmul2_rn(a, b);
+  e = __ffma2_rn(a, b, neg2(p));
+}
+__device__ __forceinline__ void two_sum1(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Exact binary32 -> binary64 by integer moves (zero and subnormal inputs give
+// 0, which is far below the precision of any value they are added to).
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned mag = b & 0x7fffffffu;
+  if (mag < 0x00800000u) return 0.0;
+  return __hiloint2double((int)((b & 0x80000000u) | ((mag >> 3) + 0x38000000u)), (int)(b << 29));
+}
+
+// One tile entry: j = 2k, 2k+1 as H = (xh0, xh1, yh0, yh1), H2 = (zh0, zh1, mh0, mh1),
+// L, L2 the matching low parts.  (nxh, nxl, ...) are the negated float-float
+// i coordinates in both halves; the four float-float accumulators get the
+// terms m_j d_ij / w_ij (x, y, z) and m_j / sqrt(d^2 + eps^2).
+template <bool MASK>
+__device__ __forceinline__ void body_ff(const float4 &H, const float4 &H2, const float4 &L,
+                                        const float4 &L2, float2 nxh, float2 nxl, float2 nyh,
+                                        float2 nyl, float2 nzh, float2 nzl, float2 e2h, float2 e2l,
+                                        float2 (&ah)[4], float2 (&al)[4], bool self0, bool self1) {
+  float2 dh[3], dl[3];
+  {
+    const float2 jh[3] = {f2(H.x, H.y), f2(H.z, H.w), f2(H2.x, H2.y)};
+    const float2 jl[3] = {f2(L.x, L.y), f2(L.z, L.w), f2(L2.x, L2.y)};
+    const float2 ih[3] = {nxh, nyh, nzh}, il[3] = {nxl, nyl, nzl};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {  // d = (jh + jl) - (ih + il), renormalised
+      float2 s, e;
+      two_sum2(jh[c], ih[c], s, e);
+      const float2 t = __fadd2_rn(__fadd2_rn(jl[c], il[c]), e);
+      two_sum2(s, t, dh[c], dl[c]);
+    }
+  }
+  // r2 = |d|^2 + eps^2
+  float2 p[3], pe[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    two_prod2(dh[c], dh[c], p[c], pe[c]);
+    pe[c] = __ffma2_rn(__fadd2_rn(dh[c], dh[c]), dl[c], pe[c]);
+  }
+  float2 s1, e1, s2, e2, s3, e3;
+  two_sum2(p[0], p[1], s1, e1);
+  two_sum2(s1, p[2], s2, e2);
+  two_sum2(s2, e2h, s3, e3);
+  const float2 lo = __fadd2_rn(__fadd2_rn(__fadd2_rn(pe[0], pe[1]), __fadd2_rn(pe[2], e2l)),
+                               __fadd2_rn(__fadd2_rn(e1, e2), e3));
+  float2 r2h, r2l;
+  fast_two_sum2(s3, lo, r2h, r2l);
+  float2 mh = f2(H2.z, H2.w), ml = f2(L2.z, L2.w);
+  if (MASK) {
+    if (self0) {
+      r2h.x = 1.0f;
+      r2l.x = 0.0f;
+      mh.x = ml.x = 0.0f;
+    }
+    if (self1) {
+      r2h.y = 1.0f;
+      r2l.y = 0.0f;
+      mh.y = ml.y = 0.0f;
+    }
+  }
+  // y = r2^{-1/2}: SFU seed y0, residual e = 1 - r2 y0^2 in float-float,
+  // y = y0 (1 + e/2 + 3 e^2 / 8) = y0 + y0 e (1/2 + 3e/8)
+  const float2 y0 = f2(rsqrt_approx(r2h.x), rsqrt_approx(r2h.y));
+  float2 th, tl, u, ue;
+  two_prod2(y0, y0, th, tl);
+  two_prod2(r2h, th, u, ue);
+  const float2 cross = __ffma2_rn(r2h, tl, __fmul2_rn(r2l, th));
+  const float2 e = fsub2(fsub2(fsub2(f2(1.0f, 1.0f), u), ue), cross);
+  const float2 yl = __fmul2_rn(__fmul2_rn(y0, e), __ffma2_rn(e, f2(0.375f, 0.375f), f2(0.5f, 0.5f)));
+  // q = y^2, a = m y, b = a q = m y^3
+  float2 q, qe, a, ae, b, be;
+  two_prod2(y0, y0, q, qe);
+  const float2 ql = __ffma2_rn(__fadd2_rn(y0, y0), yl, qe);
+  two_prod2(mh, y0, a, ae);
+  const float2 al_ = __ffma2_rn(mh, yl, __ffma2_rn(ml, y0, ae));
+  two_prod2(a, q, b, be);
+  const float2 bl = __ffma2_rn(a, ql, __ffma2_rn(al_, q, be));
+  // accumulate d b (three components) and a
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    float2 th2, tl2;
+    if (c < 3) {
+      float2 ce;
+      two_prod2(dh[c], b, th2, ce);
+      tl2 = __ffma2_rn(dh[c], bl, __ffma2_rn(dl[c], b, ce));
+    } else {
+      th2 = a;
+      tl2 = al_;
+    }
+    float2 s, es;
+    two_sum2(ah[c], th2, s, es);
+    fast_two_sum2(s, __fadd2_rn(al[c], __fadd2_rn(es, tl2)), ah[c], al[c]);
+  }
+}
+
+// Stage j-particles [jt, jt+cnt) of `src` (two float4 per particle: hi
+// (x, y, z, m), lo (x, y, z, m)) as pairs; odd tail padded as in load_pairs.
+template <int BT, int T>
+__device__ __forceinline__ void load_pairs_ff(const float4 *__restrict__ src, int64_t jt, int cnt,
+                                              float4 *tH, float4 *tH2, float4 *tL, float4 *tL2) {
+  const float4 dh = make_float4(1e18f, 1e18f, 1e18f, 0.0f), dl = make_float4(0, 0, 0, 0);
+  for (int k = threadIdx.x; 2 * k < cnt; k += BT) {
+    const float4 ah = src[2 * (jt + 2 * k)], alo = src[2 * (jt + 2 * k) + 1];
+    const bool hb = 2 * k + 1 < cnt;
+    const float4 bh = hb ? src[2 * (jt + 2 * k + 1)] : dh;
+    const float4 blo = hb ? src[2 * (jt + 2 * k + 1) + 1] : dl;
+    tH[k] = make_float4(ah.x, bh.x, ah.y, bh.y);
+    tH2[k] = make_float4(ah.z, bh.z, ah.w, bh.w);
+    tL[k] = make_float4(alo.x, blo.x, alo.y, blo.y);
+    tL2[k] = make_float4(alo.z, blo.z, alo.w, blo.w);
+  }
+}
+
+// F64E force: i coordinates re-centred on each j-tile's anchor in float-float
+// (from the particle's own float-float and the anchor's), pair terms and
+// per-tile partial sums in float-float, folded into binary64 once per tile.
+template <int BT, int R, int T, class W>
+__global__ void __launch_bounds__(BT) k_force_f64e(const d4 *__restrict__ posm,
+                                                   const float4 *__restrict__ jff,
+                                                   const float4 *__restrict__ anchor, W work,
+                                                   d4 *__restrict__ part) {
+  __shared__ float4 tH[T / 2], tH2[T / 2], tL[T / 2], tL2[T / 2];
+  for (int64_t uk = work.first(); uk < work.count(); uk += work.stride()) {
+    const Unit u = work.get(uk);
+    const int tid = threadIdx.x;
+    const int64_t j1 = u.j0 + u.nj;
+    const float e2hs = (float)u.eps2;
+    const float e2ls = (float)(u.eps2 - (double)e2hs);
+    const float2 e2h = f2(e2hs, e2hs), e2l = f2(e2ls, e2ls);
+    float xh[R][3], xl[R][3];
+    double acc[R][4];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int li = r * BT + tid;
+      const d4 p = posm[u.i0 + (li < u.ni ? li : 0)];
+      const double c3[3] = {p.x, p.y, p.z};
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        xh[r][c] = __double2float_rn(c3[c]);
+        xl[r][c] = __double2float_rn(c3[c] - (double)xh[r][c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; c++) acc[r][c] = 0.0;
+    }
+    for (int64_t jt = u.j0; jt < j1; jt += T) {
+      const int cnt = (int)min((int64_t)T, j1 - jt);
+      __syncthreads();
+      load_pairs_ff<BT, T>(jff, jt, cnt, tH, tH2, tL, tL2);
+      __syncthreads();
+      const int64_t tt = u.anchor + (jt - u.j0) / T;
+      const float4 ch = anchor[2 * tt], cl = anchor[2 * tt + 1];
+      const float chv[3] = {ch.x, ch.y, ch.z}, clv[3] = {cl.x, cl.y, cl.z};
+      float2 nh[R][3], nl[R][3], ah[R][4], al[R][4];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {  // -(x_i - c_t) as float-float
+          float s, e;
+          two_sum1(xh[r][c], -chv[c], s, e);
+          const float t = __fadd_rn(__fsub_rn(xl[r][c], clv[c]), e);
+          float h, l;
+          two_sum1(s, t, h, l);
+          nh[r][c] = f2(-h, -h);
+          nl[r][c] = f2(-l, -l);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) ah[r][c] = al[r][c] = f2(0.0f, 0.0f);
+      }
+      const int np = (cnt + 1) / 2;
+      const bool diag = (jt < u.i0 + u.ni) && (jt + cnt > u.i0);
+      if (cnt == T && !diag) {
+        for (int k = 0; k < T / 2; k++) {
+          const float4 H = tH[k], H2 = tH2[k], L = tL[k], L2 = tL2[k];
+#pragma unroll
+          for (int r = 0; r < R; r++)
+            body_ff<false>(H, H2, L, L2, nh[r][0], nl[r][0], nh[r][1], nl[r][1], nh[r][2],
+                           nl[r][2], e2h, e2l, ah[r], al[r], false, false);
+        }
+      } else {
+        for (int k = 0; k < np; k++) {
+          const float4 H = tH[k], H2 = tH2[k], L = tL[k], L2 = tL2[k];
+          const int64_t j = jt + 2 * k;
+#pragma unroll
+          for (int r = 0; r < R; r++) {
+            const int64_t i = u.i0 + r * BT + tid;
+            body_ff<true>(H, H2, L, L2, nh[r][0], nl[r][0], nh[r][1], nl[r][1], nh[r][2],
+                          nl[r][2], e2h, e2l, ah[r], al[r], j == i, j + 1 == i);
+          }
+        }
+      }
+      // fold the tile: even + odd lanes in float-float, then into binary64
+#pragma unroll
+      for (int r = 0; r < R; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          float s, e;
+          two_sum1(ah[r][c].x, ah[r][c].y, s, e);
+          const float l = __fadd_rn(__fadd_rn(al[r][c].x, al[r][c].y), e);
+          acc[r][c] += f2d_exact(s) + f2d_exact(l);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int li = r * BT + tid;
+      if (li < u.ni) part[u.out + li] = d4{acc[r][0], acc[r][1], acc[r][2], acc[r][3]};
+    }
+  }
+}
+
 // ---------------------------------------------------------------- mixed
 // fpos[j] = (x_j - c_t, y_j - c_t, z_j - c_t, m_j) in binary32, c_t the anchor of
 // j's tile; anchor[2t] = float hi part of c_t, anchor[2t+1] = float lo part.
@@ -349,7 +599,9 @@ struct TablePrep {
   __device__ __forceinline__ PrepUnit get() const { return units[blockIdx.x]; }
 };
 
-template <int BT, class W>
+// FF = true (F64E): the re-centred coordinates and the mass are written as
+// float-float, two float4 per particle (hi x, y, z, m; lo x, y, z, m).
+template <int BT, class W, bool FF>
 __global__ void __launch_bounds__(BT) k_mixed_prep(const d4 *__restrict__ posm, W work,
                                                    float4 *__restrict__ fpos,
                                                    float4 *__restrict__ anchor) {
@@ -383,9 +635,19 @@ __global__ void __launch_bounds__(BT) k_mixed_prep(const d4 *__restrict__ posm, 
     }
     c[q] = v[(cnt - 1) / 2];
   }
-  if (tid < cnt)
-    fpos[j0 + tid] = make_float4(__double2float_rn(p.x - c[0]), __double2float_rn(p.y - c[1]),
-                                 __double2float_rn(p.z - c[2]), __double2float_rn(p.w));
+  if (tid < cnt) {
+    const double dx = p.x - c[0], dy = p.y - c[1], dz = p.z - c[2];
+    const float hx = __double2float_rn(dx), hy = __double2float_rn(dy), hz = __double2float_rn(dz),
+                hm = __double2float_rn(p.w);
+    if (FF) {
+      fpos[2 * (j0 + tid)] = make_float4(hx, hy, hz, hm);
+      fpos[2 * (j0 + tid) + 1] =
+          make_float4(__double2float_rn(dx - (double)hx), __double2float_rn(dy - (double)hy),
+                      __double2float_rn(dz - (double)hz), __double2float_rn(p.w - (double)hm));
+    } else {
+      fpos[j0 + tid] = make_float4(hx, hy, hz, hm);
+    }
+  }
   if (tid == 0) {
     const float hx = __double2float_rn(c[0]), hy = __double2float_rn(c[1]),
                 hz = __double2float_rn(c[2]);
@@ -459,15 +721,18 @@ __global__ void __launch_bounds__(BT) k_force_f32(const float4 *__restrict__ pos
 // Fixed block and tile sizes per arithmetic; R is chosen at run time.
 constexpr int BT_F64 = 128, T_F64 = 128;
 constexpr int BT_F32 = 256, T_F32 = 256;
+constexpr int BT_FF = 128, T_FF = 256;
 
-int force_block_threads(int mode) { return mode == NBODY_FP64 ? BT_F64 : BT_F32; }
-int force_tile(int mode) { return mode == NBODY_FP64 ? T_F64 : T_F32; }
+int force_block_threads(int mode) {
+  return mode == NBODY_FP64 ? BT_F64 : mode == NBODY_F64E ? BT_FF : BT_F32;
+}
+int force_tile(int mode) { return mode == NBODY_FP64 ? T_F64 : mode == NBODY_F64E ? T_FF : T_F32; }
 
 bool shape_supported(int mode, const Shape &sh) {
   if (sh.r != 1 && sh.r != 2 && sh.r != 4 && sh.r != 8) return false;
+  if (mode == NBODY_F64E && sh.r == 8) return false;
   if (sh.s < 1 || sh.s > 65535) return false;
-  if (mode == NBODY_FP64) return sh.bt == BT_F64 && sh.t == T_F64;
-  return sh.bt == BT_F32 && sh.t == T_F32;
+  return sh.bt == force_block_threads(mode) && sh.t == force_tile(mode);
 }
 
 template <int R>
@@ -475,6 +740,7 @@ static const void *kernel_for(int mode) {
   switch (mode) {
     case NBODY_FP64: return (const void *)k_force_f64<BT_F64, R, T_F64, DenseWork>;
     case NBODY_MIXED: return (const void *)k_force_mixed<BT_F32, R, T_F32, DenseWork>;
+    case NBODY_F64E: return (const void *)k_force_f64e<BT_FF, (R < 4 ? R : 4), T_FF, DenseWork>;
     default: return (const void *)k_force_f32<BT_F32, R, T_F32, DenseWork>;
   }
 }
@@ -504,6 +770,10 @@ static void launch_rw(int mode, const void *posm, const float4 *fpos, const floa
   } else if (mode == NBODY_MIXED) {
     k_force_mixed<BT_F32, R, T_F32, W><<<grid, BT_F32, 0, st>>>((const d4 *)posm, fpos, anchor, w,
                                                                 (d4 *)part);
+  } else if (mode == NBODY_F64E) {
+    constexpr int RF = R < 4 ? R : 4;
+    k_force_f64e<BT_FF, RF, T_FF, W><<<grid, BT_FF, 0, st>>>((const d4 *)posm, fpos, anchor, w,
+                                                             (d4 *)part);
   } else {
     k_force_f32<BT_F32, R, T_F32, W><<<grid, BT_F32, 0, st>>>((const float4 *)posm, w,
                                                               (float4 *)part);
@@ -553,13 +823,16 @@ cudaError_t launch_force_units(int mode, const void *posm, const float4 *fpos,
 }
 
 cudaError_t launch_mixed_prep(const d4 *posm, int64_t n, int tile, float4 *fpos, float4 *anchor,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool ff) {
   if (tile != 256) return cudaErrorInvalidValue;  // one thread per tile member
   const int64_t nt = (n + tile - 1) / tile;
   DensePrep w;
   w.n = n;
   w.tile = tile;
-  k_mixed_prep<256, DensePrep><<<(unsigned)nt, 256, 0, st>>>(posm, w, fpos, anchor);
+  if (ff)
+    k_mixed_prep<256, DensePrep, true><<<(unsigned)nt, 256, 0, st>>>(posm, w, fpos, anchor);
+  else
+    k_mixed_prep<256, DensePrep, false><<<(unsigned)nt, 256, 0, st>>>(posm, w, fpos, anchor);
   return cudaGetLastError();
 }
 
@@ -568,7 +841,7 @@ cudaError_t launch_mixed_prep_units(const d4 *posm, const PrepUnit *units, int64
   if (nunits < 1 || nunits > 0x7fffffff) return cudaErrorInvalidValue;
   TablePrep w;
   w.units = units;
-  k_mixed_prep<256, TablePrep><<<(unsigned)nunits, 256, 0, st>>>(posm, w, fpos, anchor);
+  k_mixed_prep<256, TablePrep, false><<<(unsigned)nunits, 256, 0, st>>>(posm, w, fpos, anchor);
   return cudaGetLastError();
 }
 

@@ -88,8 +88,9 @@ cudaError_t launch_mixed_prep_units(const d4 *posm, const PrepUnit *units, int64
                                     float4 *fpos, float4 *anchor, cudaStream_t st);
 int force_block_threads(int mode);
 int force_tile(int mode);
+// ff: write float-float re-centred coordinates (F64E, two float4 per particle)
 cudaError_t launch_mixed_prep(const d4 *posm, int64_t n, int tile, float4 *fpos, float4 *anchor,
-                              cudaStream_t st);
+                              cudaStream_t st, bool ff = false);
 int force_max_blocks_per_sm(int mode, const Shape &sh);
 bool shape_supported(int mode, const Shape &sh);
 

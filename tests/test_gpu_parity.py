@@ -298,3 +298,49 @@ def test_fp64_and_mixed_disk_halo_2_20_sampled(nb):
     ok, err, amag = fp64_accel_gate(acc[rows], acc_o, smag, n)
     assert ok.all()
     assert np.all(np.abs(pot[rows] - pot_o) <= 1e-12 * np.abs(pot_o))
+
+
+# ------------------------------------------------------------------ F64E (float-float, binary64-class)
+def _f64e_errors(nb, pos, mass, eps, G=1.0, rows=None):
+    n = len(mass)
+    with nb.Simulation(n, "f64e", eps=eps, G=G) as sim:
+        acc, pot = sim.accel(pos, mass)
+    acc_o, pot_o, smag = oracle.accel(pos, mass, eps, G, rows=rows)
+    a = acc if rows is None else acc[rows]
+    p = pot if rows is None else pot[rows]
+    ok, err, amag = fp64_accel_gate(a, acc_o, smag, n)
+    rel = err / np.maximum(amag, 1e-300)
+    prel = np.abs(p - pot_o) / np.abs(pot_o)
+    return ok, rel, err / np.maximum(smag, 1e-300), prel
+
+
+@pytest.mark.parametrize("n", [2, 3, 129, 1000, 5003])
+@pytest.mark.parametrize("eps", [0.01, 0.0])
+def test_f64e_accel_sizes(nb, n, eps):
+    pos, _, _ = nbody_ics.plummer(n, 11 + n)
+    mass = nbody_ics.lognormal_masses(n, 12 + n)
+    ok, rel, rels, prel = _f64e_errors(nb, pos, mass, eps, 1.3)
+    print(f"f64e n={n} eps={eps}: gate {ok.mean():.3f} rel max {rel.max():.2e} rms "
+          f"{np.sqrt((rel ** 2).mean()):.2e} |da|/S max {rels.max():.2e} pot {prel.max():.2e}")
+    assert ok.all() and prel.max() <= 1e-12          # the FP64 gate
+
+
+def test_f64e_disk_halo_sampled(nb):
+    n = 2 ** 17
+    w = nbody_ics.workload("disk_halo", n=n)
+    rows = np.random.default_rng(2).choice(n, 256, replace=False)
+    ok, rel, rels, prel = _f64e_errors(nb, w["pos"], w["mass"], w["eps"], rows=rows)
+    print(f"f64e disk_halo 2^17: gate {ok.mean():.3f} rel max {rel.max():.2e} rms "
+          f"{np.sqrt((rel ** 2).mean()):.2e} |da|/S max {rels.max():.2e} pot {prel.max():.2e}")
+    assert ok.all() and prel.max() <= 1e-12          # the FP64 gate
+
+
+def test_f64e_kdk_tracks_oracle(nb):
+    w = nbody_ics.workload("plummer", n=2048)
+    with nb.Simulation(2048, "f64e", eps=0.01) as sim:
+        sim.set_state(w["pos"], w["vel"], w["mass"])
+        sim.step(1e-3, 10)
+        p, v, _, _ = sim.get_state()
+    op, ov, _, _ = oracle.kdk(w["pos"], w["vel"], w["mass"], 0.01, 1.0, 1e-3, 10)
+    assert np.abs(p - op).max() <= 1e-12 * np.abs(op).max()
+    assert np.abs(v - ov).max() <= 1e-11 * np.abs(ov).max()
