@@ -226,7 +226,7 @@ def e2e_mode(nb, torch, w, mode, steps, warmup):
                 d2h=acc.numel() * 8 + pot.numel() * 8)
 
 
-def run_serving(args):
+def run_serving(args, fp64_kernel="fp64"):
     """Serving workload: Poisson arrivals (200/s) of independent Plummer or
     disk + halo simulations, N log-uniform in [2^10, 2^16], FP64 or MIXED
     50/50, 100 KDK steps each, through the continuous-batching server for a
@@ -237,14 +237,15 @@ def run_serving(args):
     reqs = serve.poisson_requests(int(200 * args.serve_seconds) + 1, rate=200.0, seed=20180115,
                                   nsteps=100, dt=DT)
     srv = serve.Server(capacity={"fp64": 2 ** 20, "mixed": 2 ** 22},
-                       max_sims={"fp64": 16, "mixed": 64}, autotune=True, keep_state=False)
+                       max_sims={"fp64": 16, "mixed": 64}, autotune=True, keep_state=False,
+                       fp64_kernel=fp64_kernel)
     out = srv.run(reqs, duration=args.serve_seconds)
     srv.close()
     out.pop("done")
     out["workload"] = ("Poisson 200 req/s; N log-uniform [2^10, 2^16]; Plummer (eps 0.01) or disk+halo "
                        "(eps 0.02) 50/50; FP64 or mixed 50/50; 100 KDK steps dt=5e-4; seed 20180115")
-    out["pools"] = {"fp64": {"capacity": 2 ** 20, "max_sims": 16},
-                    "mixed": {"capacity": 2 ** 22, "max_sims": 64}}
+    out["pools"] = {"fp64": {"capacity": 2 ** 20, "max_sims": 16, "kernel": fp64_kernel},
+                    "mixed": {"capacity": 2 ** 22, "max_sims": 64, "kernel": "mixed"}}
     return out
 
 
@@ -280,6 +281,7 @@ def run_gpu(args):
     e2e64 = e2e_mode(nb, torch, w, "fp64", steps=args.e2e_steps, warmup=1)
     e2emx = e2e_mode(nb, torch, w, "mixed", steps=max(args.steps, 3), warmup=args.warmup)
     serving = run_serving(args) if args.serve_seconds > 0 else None
+    serving_f64e = run_serving(args, fp64_kernel="f64e") if args.serve_seconds > 0 else None
 
     if rank != 0:
         if world > 1:
@@ -376,6 +378,7 @@ def run_gpu(args):
                                    "f64e": drift(f64e["diag0"], f64e["diags"]),
                                    "mixed": drift(mixed["diag0"], mixed["diags"])},
         "serving": serving,
+        "serving_fp64_requests_on_f64e": serving_f64e,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -53,8 +53,7 @@ extern "C" {
 #define NBODY_FP32  2  /* binary32 throughout, state included: the paper's single precision (SP) */
 #define NBODY_F64E  3  /* binary64-class accuracy from float-float (about 48-bit) arithmetic on
                           the binary32 pipes, on coordinates re-centred per j-tile; tile partial
-                          sums folded into binary64; state and update in binary64.  Not offered
-                          by the batch interface. */
+                          sums folded into binary64; state and update in binary64. */
 
 /* ---- time integration schemes ------------------------------------------ */
 #define NBODY_KDK 0    /* Eq. 5-7 (section 1): predictor, drift, one force evaluation, corrector */
@@ -191,7 +190,8 @@ int nbody_profile_read(nbody_ctx *ctx, double *force_ms, int64_t *force_launches
  * A batch is a device pool of `capacity` particles shared by up to
  * `max_sims` resident simulations of uneven size.  Each simulation runs the
  * KDK leapfrog of Eq. 5-7 over the Eq. 1-2 force sum with its own n, eps, G,
- * dt and mode (NBODY_FP64 or NBODY_MIXED; NBODY_FP32 is not offered here).
+ * dt and mode (NBODY_FP64, NBODY_MIXED or NBODY_F64E; NBODY_FP32 is not
+ * offered here).
  * One tick (nbody_batch_step) advances every resident simulation by one
  * step in a few launches whose thread blocks are work units of single
  * simulations, so small and large simulations share the GPU.  A simulation's
@@ -272,10 +272,10 @@ int nbody_batch_set_fp64_residency(nbody_batch *b, int blocks_per_sm);
 int nbody_batch_profile(nbody_batch *b, int enable);
 
 /* Synchronise and return, for up to `cap` ticks recorded since the last
- * read: tick_ms[k] (whole tick), force_ms[2k], force_ms[2k+1] (the FP64 and
- * MIXED force launches, 0 when absent), inter[2k], inter[2k+1] (their
- * interactions, n^2 summed over simulations); *nticks = ticks recorded.
- * Any array may be NULL; the record is cleared. */
+ * read: tick_ms[k] (whole tick), force_ms[3k..3k+2] (the FP64, MIXED and
+ * F64E force launches, 0 when absent), inter[3k..3k+2] (their interactions,
+ * n^2 summed over simulations); *nticks = ticks recorded.  Any array may be
+ * NULL; the record is cleared. */
 int nbody_batch_profile_read(nbody_batch *b, int64_t cap, double *tick_ms, double *force_ms,
                              double *inter, int64_t *nticks);
 

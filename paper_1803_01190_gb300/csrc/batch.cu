@@ -1,7 +1,7 @@
 // Batched (continuous-batching) execution of many independent simulations of
 // uneven size: the serving path.  Each simulation is the paper's KDK leapfrog
 // (Eq. 5-7) over the Eq. 1-2 force sum, with its own N, softening, G, time
-// step and precision mode (FP64 or MIXED).
+// step and precision mode (FP64, MIXED or F64E).
 //
 // All resident simulations share one device pool of `capacity` particles.
 // A simulation occupies a contiguous range of it; ranges are handed out first
@@ -39,6 +39,8 @@ namespace {
 constexpr int SMAX = 16;       // most j-segments per simulation
 constexpr int ALIGN = 64;      // pool ranges start on 64-particle boundaries
 constexpr int FL_ACTIVE = 1, FL_INIT = 2;
+constexpr int NCLS = 3;  // kernel classes: FP64, MIXED, F64E
+int cls_of(int mode) { return mode == NBODY_MIXED ? 1 : mode == NBODY_F64E ? 2 : 0; }
 
 struct SimDesc {
   int64_t off, n, part;
@@ -134,7 +136,7 @@ struct nbody_batch {
   int64_t cap = 0;
   int max_sims = 0;
   d4 *R = nullptr, *F = nullptr, *V = nullptr, *VB = nullptr, *A = nullptr, *part = nullptr;
-  float4 *fpos = nullptr, *anchor = nullptr;
+  float4 *fpos = nullptr, *fposff = nullptr, *anchor = nullptr;  // MIXED / F64E staging
   int32_t *sim_of = nullptr;
   double *diag_blocks = nullptr, *diag_out = nullptr, *h_diag = nullptr;
   double *stage = nullptr;  // device scratch for unpacking (cap x 6 doubles)
@@ -146,7 +148,7 @@ struct nbody_batch {
   int64_t units_cap = 0, prep_cap = 0;
   int tb = 0;
   bool dirty = true;
-  int64_t n64 = 0, nmx = 0, nprep = 0, hi = 0;  // current table sizes and pool high-water mark
+  int64_t n64 = 0, nmx = 0, nfe = 0, nprep = 0, nprepfe = 0, hi = 0;  // table sizes, pool high-water mark
   // admission staging (pinned host ring)
   static constexpr int RING = 4;
   double *h_in[RING] = {};
@@ -156,13 +158,13 @@ struct nbody_batch {
   // host state
   std::vector<SimHost> sims;
   std::map<int64_t, int64_t> free_ranges;  // offset -> length
-  int r_mode[2] = {2, 2};                  // R per mode (FP64, MIXED)
-  int fp64_per_sm = 2;                     // resident FP64 force blocks per SM (persistent grid)
-  int64_t seg_mode[2] = {4096, 8192};      // target j-segment length per mode
+  int r_mode[3] = {2, 2, 2};                 // R per kernel class (FP64, MIXED, F64E)
+  int fp64_per_sm = 2;                       // resident FP64 force blocks per SM (persistent grid)
+  int64_t seg_mode[3] = {4096, 8192, 4096};  // target j-segment length per class
   // profiling
-  std::vector<cudaEvent_t> evs;  // 6 per tick: tick start/end, f64 start/end, mixed start/end
+  std::vector<cudaEvent_t> evs;  // 8 per tick: tick start/end, then start/end per class
   size_t ev_used = 0;
-  std::vector<double> tick_inter[2];
+  std::vector<double> tick_inter[3];
   int64_t launches = 0;
   bool prof = false;
 };
@@ -248,8 +250,8 @@ int ensure_tables(nbody_batch *b, int64_t nunits, int64_t nprep) {
 // Rebuild the work-unit tables of the resident simulations into the spare
 // buffer and upload them (stream-ordered before the next tick).
 int build_tables(nbody_batch *b) {
-  std::vector<nb::Unit> u64, umx;
-  std::vector<nb::PrepUnit> prep;
+  std::vector<nb::Unit> uc[NCLS];
+  std::vector<nb::PrepUnit> prep, prepfe;
   const int nsl = b->max_sims;
   const int nb_buf = 1 - b->tb;
   BCK(cudaEventSynchronize(b->tab_ev[nb_buf]));  // its previous upload has been consumed
@@ -259,7 +261,7 @@ int build_tables(nbody_batch *b) {
     const SimHost &h = b->sims[s];
     SimDesc d = {};
     if (h.used && h.active) {
-      const int m = h.mode == NBODY_MIXED ? 1 : 0;
+      const int m = cls_of(h.mode);
       const int bt = nb::force_block_threads(h.mode), T = nb::force_tile(h.mode);
       const int64_t pb = (int64_t)bt * b->r_mode[m];
       int64_t seg = std::max<int64_t>(T, round_up(b->seg_mode[m], T));
@@ -283,7 +285,7 @@ int build_tables(nbody_batch *b) {
           u.out = pbase + (int64_t)k * h.n + ib;
           u.anchor = abase + (int64_t)k * seg / T;
           u.eps2 = h.eps * h.eps;
-          (m ? umx : u64).push_back(u);
+          uc[m].push_back(u);
         }
       if (m) {
         for (int64_t t = 0; t * T < h.n; t++) {
@@ -292,7 +294,7 @@ int build_tables(nbody_batch *b) {
           p.cnt = (int32_t)std::min<int64_t>(T, h.n - t * T);
           p.anchor = abase + t;
           p.pad = 0;
-          prep.push_back(p);
+          (m == 1 ? prep : prepfe).push_back(p);
         }
         abase += (h.n + T - 1) / T;
       }
@@ -305,25 +307,31 @@ int build_tables(nbody_batch *b) {
   auto by_work = [](const nb::Unit &a, const nb::Unit &c) {
     return (int64_t)a.ni * a.nj > (int64_t)c.ni * c.nj;
   };
-  std::stable_sort(u64.begin(), u64.end(), by_work);
-  std::stable_sort(umx.begin(), umx.end(), by_work);
-  int rc = ensure_tables(b, (int64_t)(u64.size() + umx.size()), (int64_t)prep.size());
+  for (int m = 0; m < NCLS; m++) std::stable_sort(uc[m].begin(), uc[m].end(), by_work);
+  const int64_t nu = (int64_t)(uc[0].size() + uc[1].size() + uc[2].size());
+  const int64_t np = (int64_t)(prep.size() + prepfe.size());
+  int rc = ensure_tables(b, nu, np);
   if (rc) return rc;
   nb::Unit *hu = b->h_units[nb_buf];
-  std::copy(u64.begin(), u64.end(), hu);
-  std::copy(umx.begin(), umx.end(), hu + u64.size());
+  int64_t at = 0;
+  for (int m = 0; m < NCLS; m++) {
+    std::copy(uc[m].begin(), uc[m].end(), hu + at);
+    at += (int64_t)uc[m].size();
+  }
   std::copy(prep.begin(), prep.end(), b->h_prep[nb_buf]);
-  const int64_t nu = (int64_t)(u64.size() + umx.size());
+  std::copy(prepfe.begin(), prepfe.end(), b->h_prep[nb_buf] + prep.size());
   if (nu) BCK(cudaMemcpyAsync(b->d_units[nb_buf], hu, nu * sizeof(nb::Unit), cudaMemcpyHostToDevice, b->st));
-  if (!prep.empty())
-    BCK(cudaMemcpyAsync(b->d_prep[nb_buf], b->h_prep[nb_buf], prep.size() * sizeof(nb::PrepUnit),
+  if (np)
+    BCK(cudaMemcpyAsync(b->d_prep[nb_buf], b->h_prep[nb_buf], np * sizeof(nb::PrepUnit),
                         cudaMemcpyHostToDevice, b->st));
   BCK(cudaMemcpyAsync(b->d_sims[nb_buf], hs, nsl * sizeof(SimDesc), cudaMemcpyHostToDevice, b->st));
   BCK(cudaEventRecord(b->tab_ev[nb_buf], b->st));
   b->tb = nb_buf;
-  b->n64 = (int64_t)u64.size();
-  b->nmx = (int64_t)umx.size();
+  b->n64 = (int64_t)uc[0].size();
+  b->nmx = (int64_t)uc[1].size();
+  b->nfe = (int64_t)uc[2].size();
   b->nprep = (int64_t)prep.size();
+  b->nprepfe = (int64_t)prepfe.size();
   b->hi = hi;
   b->dirty = false;
   return NBODY_OK;
@@ -345,7 +353,7 @@ int check_slot(nbody_batch *b, int slot) {
 }
 
 void free_batch(nbody_batch *b) {
-  void *dp[] = {b->R, b->F, b->V, b->VB, b->A, b->part, b->fpos, b->anchor, b->sim_of,
+  void *dp[] = {b->R, b->F, b->V, b->VB, b->A, b->part, b->fpos, b->fposff, b->anchor, b->sim_of,
                 b->diag_blocks, b->diag_out, b->stage, b->d_units[0], b->d_units[1],
                 b->d_prep[0], b->d_prep[1], b->d_sims[0], b->d_sims[1]};
   for (void *p : dp)
@@ -370,7 +378,7 @@ extern "C" {
 const char *nbody_batch_last_error(void) { return g_msg; }
 
 int64_t nbody_batch_bytes_per_particle(void) {
-  return 5 * (int64_t)sizeof(d4) + SMAX * (int64_t)sizeof(d4) + (int64_t)sizeof(float4) +
+  return 5 * (int64_t)sizeof(d4) + SMAX * (int64_t)sizeof(d4) + 3 * (int64_t)sizeof(float4) +
          (int64_t)sizeof(int32_t) + 6 * (int64_t)sizeof(double);
 }
 
@@ -401,6 +409,7 @@ int nbody_batch_create(nbody_batch **out, int64_t capacity, int max_sims, void *
             cudaMalloc(&b->A, c * sizeof(d4)) == cudaSuccess &&
             cudaMalloc(&b->part, c * SMAX * sizeof(d4)) == cudaSuccess &&
             cudaMalloc(&b->fpos, c * sizeof(float4)) == cudaSuccess &&
+            cudaMalloc(&b->fposff, 2 * c * sizeof(float4)) == cudaSuccess &&
             cudaMalloc(&b->anchor, (size_t)tiles * 2 * sizeof(float4)) == cudaSuccess &&
             cudaMalloc(&b->sim_of, c * sizeof(int32_t)) == cudaSuccess &&
             cudaMalloc(&b->stage, c * 6 * sizeof(double)) == cudaSuccess &&
@@ -442,7 +451,8 @@ int nbody_batch_admit(nbody_batch *b, int64_t n, int mode, double eps, double G,
   if (!b || !slot) return bfail(NBODY_EINVAL, "NULL argument");
   *slot = -1;
   if (n < 1) return bfail(NBODY_EINVAL, "n < 1");
-  if (mode != NBODY_FP64 && mode != NBODY_MIXED) return bfail(NBODY_EINVAL, "batch modes: FP64 or MIXED");
+  if (mode != NBODY_FP64 && mode != NBODY_MIXED && mode != NBODY_F64E)
+    return bfail(NBODY_EINVAL, "batch modes: FP64, MIXED or F64E");
   if (!(eps >= 0) || !std::isfinite(eps) || !std::isfinite(G)) return bfail(NBODY_EINVAL, "eps or G");
   if (!(dt > 0) || !std::isfinite(dt)) return bfail(NBODY_EINVAL, "dt must be finite and > 0");
   if (!pos || !mass) return bfail(NBODY_EINVAL, "NULL pos or mass");
@@ -536,10 +546,10 @@ int nbody_batch_step(nbody_batch *b, int64_t nticks) {
       int rc = build_tables(b);
       if (rc) return rc;
     }
-    if (b->n64 + b->nmx == 0) return NBODY_OK;
-    cudaEvent_t e[6] = {};
+    if (b->n64 + b->nmx + b->nfe == 0) return NBODY_OK;
+    cudaEvent_t e[2 + 2 * NCLS] = {};
     if (b->prof)
-      for (int k = 0; k < 6; k++)
+      for (int k = 0; k < 2 + 2 * NCLS; k++)
         if (!(e[k] = next_event(b))) return bfail(NBODY_ECUDA, "event");
     const int tb = b->tb;
     if (b->prof) BCK(cudaEventRecord(e[0], b->st));
@@ -549,6 +559,16 @@ int nbody_batch_step(nbody_batch *b, int64_t nticks) {
       BCK(nb::launch_force_units(NBODY_MIXED, b->F, b->fpos, b->anchor, b->d_units[tb] + b->n64,
                                  b->nmx, b->r_mode[1], b->part, 0, b->st));
       if (b->prof) BCK(cudaEventRecord(e[5], b->st));
+      b->launches += 2;
+    }
+    if (b->nfe) {
+      if (b->prof) BCK(cudaEventRecord(e[6], b->st));
+      BCK(nb::launch_mixed_prep_units(b->F, b->d_prep[tb] + b->nprep, b->nprepfe, b->fposff,
+                                      b->anchor, b->st, true));
+      BCK(nb::launch_force_units(NBODY_F64E, b->F, b->fposff, b->anchor,
+                                 b->d_units[tb] + b->n64 + b->nmx, b->nfe, b->r_mode[2], b->part, 0,
+                                 b->st));
+      if (b->prof) BCK(cudaEventRecord(e[7], b->st));
       b->launches += 2;
     }
     if (b->n64) {
@@ -569,10 +589,10 @@ int nbody_batch_step(nbody_batch *b, int64_t nticks) {
     if (b->prof) BCK(cudaEventRecord(e[1], b->st));
     // bookkeeping: every active simulation advanced one step, except first ticks (a(t0) only)
     bool any_init = false;
-    double inter[2] = {0, 0};
+    double inter[NCLS] = {0, 0, 0};
     for (auto &h : b->sims) {
       if (!(h.used && h.active)) continue;
-      inter[h.mode == NBODY_MIXED ? 1 : 0] += (double)h.n * (double)h.n;
+      inter[cls_of(h.mode)] += (double)h.n * (double)h.n;
       if (h.init) {
         h.init = false;
         any_init = true;
@@ -583,6 +603,7 @@ int nbody_batch_step(nbody_batch *b, int64_t nticks) {
     if (b->prof) {
       b->tick_inter[0].push_back(b->n64 ? inter[0] : 0);
       b->tick_inter[1].push_back(b->nmx ? inter[1] : 0);
+      b->tick_inter[2].push_back(b->nfe ? inter[2] : 0);
     }
     if (any_init) b->dirty = true;  // the INIT flags must be cleared in the device table
   }
@@ -697,10 +718,10 @@ int nbody_batch_slot_info(nbody_batch *b, int slot, int64_t *n, int *mode, int64
 
 int nbody_batch_set_launch(nbody_batch *b, int mode, int ipt, int64_t seg) {
   if (!b) return bfail(NBODY_EINVAL, "NULL batch");
-  if (mode != NBODY_FP64 && mode != NBODY_MIXED) return bfail(NBODY_EINVAL, "mode");
+  if (mode != NBODY_FP64 && mode != NBODY_MIXED && mode != NBODY_F64E) return bfail(NBODY_EINVAL, "mode");
   if (ipt != 1 && ipt != 2 && ipt != 4 && ipt != 8) return bfail(NBODY_EINVAL, "ipt");
   if (seg < 1) return bfail(NBODY_EINVAL, "seg");
-  const int m = mode == NBODY_MIXED ? 1 : 0;
+  const int m = cls_of(mode);
   if (b->r_mode[m] != ipt || b->seg_mode[m] != seg) {
     b->r_mode[m] = ipt;
     b->seg_mode[m] = seg;
@@ -722,9 +743,9 @@ int nbody_batch_profile(nbody_batch *b, int enable) {
 }
 
 // Per-tick timings since the last read (synchronises): up to `cap` ticks of
-// tick_ms (whole tick), force_ms[2*k..] (FP64, MIXED force launches, 0 when
-// absent) and inter[2*k..] (interactions of each mode in tick k).  *nticks
-// receives the number of ticks recorded (all are consumed).
+// tick_ms (whole tick), force_ms[3*k..3*k+2] (FP64, MIXED, F64E force
+// launches, 0 when absent) and inter[3*k..] (interactions of each class in
+// tick k).  *nticks receives the number of ticks recorded (all are consumed).
 int nbody_batch_profile_read(nbody_batch *b, int64_t cap, double *tick_ms, double *force_ms,
                              double *inter, int64_t *nticks) {
   if (!b) return bfail(NBODY_EINVAL, "NULL batch");
@@ -732,20 +753,19 @@ int nbody_batch_profile_read(nbody_batch *b, int64_t cap, double *tick_ms, doubl
   BCK(cudaStreamSynchronize(b->st));
   const int64_t nt = (int64_t)b->tick_inter[0].size();
   for (int64_t k = 0; k < nt && k < cap; k++) {
-    cudaEvent_t *e = &b->evs[6 * k];
+    cudaEvent_t *e = &b->evs[(2 + 2 * NCLS) * k];
     float ms = 0;
     BCK(cudaEventElapsedTime(&ms, e[0], e[1]));
     if (tick_ms) tick_ms[k] = ms;
-    for (int m = 0; m < 2; m++) {
+    for (int m = 0; m < NCLS; m++) {
       float f = 0;
       if (b->tick_inter[m][k] > 0) BCK(cudaEventElapsedTime(&f, e[2 + 2 * m], e[3 + 2 * m]));
-      if (force_ms) force_ms[2 * k + m] = f;
-      if (inter) inter[2 * k + m] = b->tick_inter[m][k];
+      if (force_ms) force_ms[NCLS * k + m] = f;
+      if (inter) inter[NCLS * k + m] = b->tick_inter[m][k];
     }
   }
   if (nticks) *nticks = nt;
-  b->tick_inter[0].clear();
-  b->tick_inter[1].clear();
+  for (int m = 0; m < NCLS; m++) b->tick_inter[m].clear();
   b->ev_used = 0;
   return NBODY_OK;
 }

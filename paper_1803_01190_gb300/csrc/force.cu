@@ -837,11 +837,14 @@ cudaError_t launch_mixed_prep(const d4 *posm, int64_t n, int tile, float4 *fpos,
 }
 
 cudaError_t launch_mixed_prep_units(const d4 *posm, const PrepUnit *units, int64_t nunits,
-                                    float4 *fpos, float4 *anchor, cudaStream_t st) {
+                                    float4 *fpos, float4 *anchor, cudaStream_t st, bool ff) {
   if (nunits < 1 || nunits > 0x7fffffff) return cudaErrorInvalidValue;
   TablePrep w;
   w.units = units;
-  k_mixed_prep<256, TablePrep, false><<<(unsigned)nunits, 256, 0, st>>>(posm, w, fpos, anchor);
+  if (ff)
+    k_mixed_prep<256, TablePrep, true><<<(unsigned)nunits, 256, 0, st>>>(posm, w, fpos, anchor);
+  else
+    k_mixed_prep<256, TablePrep, false><<<(unsigned)nunits, 256, 0, st>>>(posm, w, fpos, anchor);
   return cudaGetLastError();
 }
 

@@ -85,7 +85,7 @@ cudaError_t launch_force_units(int mode, const void *posm, const float4 *fpos,
                                const float4 *anchor, const Unit *units, int64_t nunits, int r,
                                void *part, int64_t max_blocks, cudaStream_t st);
 cudaError_t launch_mixed_prep_units(const d4 *posm, const PrepUnit *units, int64_t nunits,
-                                    float4 *fpos, float4 *anchor, cudaStream_t st);
+                                    float4 *fpos, float4 *anchor, cudaStream_t st, bool ff = false);
 int force_block_threads(int mode);
 int force_tile(int mode);
 // ff: write float-float re-centred coordinates (F64E, two float4 per particle)

@@ -22,9 +22,10 @@ import time
 
 import numpy as np
 
-from ._abi import FP64, MIXED, NbodyError, check, lib
+from ._abi import F64E, FP64, MIXED, NbodyError, check, lib
 
-MODES = {"fp64": FP64, "mixed": MIXED}
+MODES = {"fp64": FP64, "mixed": MIXED, "f64e": F64E}
+_CLS = {"fp64": 0, "mixed": 1, "f64e": 2}
 _ENOSPC = -6
 
 
@@ -139,10 +140,11 @@ class Batch:
               "nbody_batch_set_fp64_residency")
 
     def profile_read(self, cap=4096):
-        """(tick_ms (k,), force_ms (k,2), interactions (k,2)) for the ticks since the last read."""
+        """(tick_ms (k,), force_ms (k,3), interactions (k,3)) for the ticks since the last read;
+        columns: FP64, MIXED, F64E force launches."""
         tick = np.zeros(cap)
-        force = np.zeros((cap, 2))
-        inter = np.zeros((cap, 2))
+        force = np.zeros((cap, 3))
+        inter = np.zeros((cap, 3))
         k = ctypes.c_int64()
         check(lib.nbody_batch_profile_read(self._h, cap, ctypes.c_void_p(tick.ctypes.data),
                                            ctypes.c_void_p(force.ctypes.data),
@@ -212,15 +214,16 @@ class Request:
 
 
 class _Pool:
-    def __init__(self, mode, capacity, max_sims, launch):
+    def __init__(self, mode, capacity, max_sims, launch, kernel=None):
         import torch
         self.mode = mode
+        self.kernel = kernel or mode       # the batch mode the pool's simulations run in
         # MIXED ticks are short: give their stream priority so that their blocks are
         # scheduled as soon as an SM has room next to the long FP64 blocks
         self.stream = torch.cuda.Stream(priority=-1 if mode == "mixed" else 0)
         self.batch = Batch(capacity, max_sims, stream=self.stream)
         self.batch.profile(True)
-        self.batch.set_launch(mode, *launch)
+        self.batch.set_launch(self.kernel, *launch)
         self.queue = []
         self.active = {}
         self.inflight = False
@@ -246,14 +249,17 @@ class Server:
     queued counts."""
 
     def __init__(self, capacity, max_sims, autotune=True, launch=None, lookahead=8, keep_state=True,
-                 split=None, modes=("fp64", "mixed")):
+                 split=None, modes=("fp64", "mixed"), fp64_kernel="fp64"):
         """capacity: particles (split between the pools by `split`) or {mode: particles};
-        max_sims: resident simulations per pool, an int or {mode: int}."""
-        launch = launch or {"fp64": (2, 4096), "mixed": (2, 8192)}
+        max_sims: resident simulations per pool, an int or {mode: int}; fp64_kernel:
+        "fp64" (binary64 FP64 pipe) or "f64e" (binary64-class float-float on the FP32
+        pipes, within the same parity gate) for requests asking for FP64."""
+        launch = launch or {"fp64": (2, 4096), "mixed": (2, 8192), "f64e": (2, 4096)}
         split = split or {m: 1.0 / len(modes) for m in modes}
         cap = capacity if isinstance(capacity, dict) else {m: max(1, int(capacity * split[m])) for m in modes}
         ms = max_sims if isinstance(max_sims, dict) else {m: max_sims for m in modes}
-        self.pools = {m: _Pool(m, cap[m], ms[m], launch[m]) for m in modes}
+        kern = {m: (fp64_kernel if m == "fp64" else m) for m in modes}
+        self.pools = {m: _Pool(m, cap[m], ms[m], launch[kern[m]], kern[m]) for m in modes}
         self.tuner = Autotuner() if autotune else None
         self.lookahead = lookahead
         self.keep_state = keep_state
@@ -272,7 +278,7 @@ class Server:
                 i += 1                       # does not fit yet: look further down the queue
                 continue
             pos, vel, mass = rq.make()
-            slot = P.batch.admit(pos, vel, mass, rq.mode, rq.eps, rq.G, rq.dt)
+            slot = P.batch.admit(pos, vel, mass, P.kernel, rq.eps, rq.G, rq.dt)
             if slot is None:
                 i += 1
                 continue
@@ -282,7 +288,7 @@ class Server:
 
     def _finish_tick(self, P, t0, done):
         tick, force, inter = P.batch.profile_read()
-        mi = 0 if P.mode == "fp64" else 1
+        mi = _CLS[P.kernel]
         for k in range(len(tick)):
             P.ticks_ms.append(float(tick[k]))
             self._inter += float(inter[k].sum())
@@ -303,10 +309,10 @@ class Server:
         load = sum(float(rq.n) ** 2 for rq in P.active.values())
         P.chosen = None
         if self.tuner:
-            key = Autotuner.bucket(P.mode, load)
+            key = Autotuner.bucket(P.kernel, load)
             c = self.tuner.choose(key)
             P.chosen = (key, c)
-            P.batch.set_launch(P.mode, *c)
+            P.batch.set_launch(P.kernel, *c)
         P.batch.step(1)
         P.inflight = True
         P.ticks += 1

@@ -150,3 +150,46 @@ def test_server_continuous_batching_alone_vs_mix(sv):
         tol = 1e-12 if rq.mode == "fp64" else 1e-9
         assert np.abs(bp - sp).max() <= tol * np.abs(sp).max()
         assert np.abs(bv - svv).max() <= tol * np.abs(svv).max()
+
+
+def test_batch_f64e_matches_oracle_and_single(sv):
+    """F64E simulations in a pool (with FP64 and MIXED neighbours) against the
+    oracle (FP64 gate on the final accelerations, positions to 1e-12) and
+    against the same simulation in a single F64E context (same launch shape,
+    other blocking of the work: 1e-12 relative)."""
+    nb, serve = sv
+    b = serve.Batch(capacity=16384, max_sims=6)
+    p, v, m = _plummer(1200, 21)
+    s = b.admit(p, v, m, "f64e", 0.01, 1.0, 1e-3)
+    b.admit(*_plummer(900, 22), "fp64", 0.01, 1.0, 1e-3)
+    b.admit(*_plummer(700, 23), "mixed", 0.01, 1.0, 1e-3)
+    b.step(6)
+    pos, vel, t, step = b.get_state(s)
+    acc, _ = b.get_accel(s)
+    b.close()
+    op, ov, oa, _ = oracle.kdk(p, v, m, 0.01, 1.0, 1e-3, 5)
+    assert step == 5
+    assert np.abs(pos - op).max() <= 1e-12 * np.abs(op).max()
+    assert np.abs(vel - ov).max() <= 1e-11 * np.abs(ov).max()
+    _, _, smag = oracle.accel(op, m, 0.01)
+    assert fp64_accel_gate(acc, oa, smag, 1200)[0].all()
+    with nb.Simulation(1200, "f64e", eps=0.01) as sim:
+        sim.set_state(p, v, m)
+        sim.step(1e-3, 5)
+        sp, svv, _, _ = sim.get_state()
+    assert np.abs(pos - sp).max() <= 1e-12 * np.abs(sp).max()
+
+
+def test_server_fp64_requests_on_f64e(sv):
+    nb, serve = sv
+    reqs = serve.poisson_requests(8, rate=400.0, seed=6, n_range=(256, 2000), nsteps=8, dt=5e-4)
+    srv = serve.Server(capacity=2 * 8192, max_sims=4, autotune=True, fp64_kernel="f64e")
+    out = srv.run(reqs, duration=120)
+    srv.close()
+    assert out["completed"] == 8
+    for rq in out["done"]:
+        p, v, m = rq.make()
+        op, ov, _, _ = oracle.kdk(p, v, m, rq.eps, rq.G, rq.dt, rq.nsteps)
+        bp = rq.result[0]
+        tol = 1e-12 if rq.mode == "fp64" else 1e-7
+        assert np.abs(bp - op).max() <= tol * np.abs(op).max(), (rq.mode, np.abs(bp - op).max())
