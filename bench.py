@@ -39,6 +39,38 @@ FP64_PEAK_TFLOPS = SMS * FP64_PER_CLK * 2 * SM_MAX_GHZ / 1e3
 FP32_PEAK_TFLOPS = SMS * FP32_PER_CLK * 2 * SM_MAX_GHZ / 1e3
 
 
+# DRAM traffic of one FP64 force launch at N = 2^20 (dram__bytes_read.sum +
+# dram__bytes_write.sum from one full-size ncu capture; see the k_force_f64 DRAM
+# profile summary).  It is reported only while the kernel's source is the one
+# that was captured: `src_sha` hashes rsqrt_f64, body_f64 and k_force_f64.
+TRAFFIC = {"k_force_f64": {"bytes": 47.35e6 + 64.05e6, "n": 2 ** 20, "src_sha": "0b332b63cffc1655"}}
+
+
+def _kernel_src_sha(names):
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1803_01190_gb300", "csrc", "force.cu")).read()
+    parts = []
+    for start in names:
+        i = src.index(start)
+        j = src.index("{", i)
+        depth = 0
+        for k in range(j, len(src)):
+            depth += src[k] == "{"
+            depth -= src[k] == "}"
+            if depth == 0:
+                parts.append(src[i:k + 1])
+                break
+    return hashlib.sha256("\n".join(parts).encode()).hexdigest()[:16]
+
+
+def traffic_f64(n):
+    t = TRAFFIC["k_force_f64"]
+    sha = _kernel_src_sha(["__device__ __forceinline__ double rsqrt_f64(",
+                           "__device__ __forceinline__ void body_f64(",
+                           "__global__ void __launch_bounds__(BT) k_force_f64("])
+    return t["bytes"] if (sha == t["src_sha"] and n == t["n"]) else None
+
+
 def workload_desc(n):
     return (f"exponential disk (Rd=1, Rmax=5, h=0.05, Q=1.2) + live Plummer halo (a=3), 1:1, "
             f"N={n}, eps={EPS}, KDK dt={DT}, seed 20180113")
@@ -334,7 +366,10 @@ def run_gpu(args):
         "p50_step_ms": float(np.percentile(per, 50)), "p99_step_ms": float(np.percentile(per, 99)),
         "roofline": {"bound": "alu", "kernel": "k_force_f64", "achieved": achieved_tf,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": None,
+                     "traffic": traffic_f64(n),
+                     "traffic_note": "DRAM bytes per launch from one full-size ncu capture; the O(N) "
+                                     "algorithmic bytes (32 B in + S x 32 B partials out per particle) "
+                                     "mostly stay in the 129 MB L2",
                      "flop_convention": f"{FLOP_PER_INTERACTION} flop/interaction x N^2 per launch",
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
                      "force_ms_per_launch": fms, "force_share_of_step": fms / ms64},
@@ -398,6 +433,40 @@ def profile_force(args):
     print(json.dumps({"profile_force": args.profile_force, "n": args.n}))
 
 
+def run_drift(args):
+    """Conservation over a long run on the disk + halo model, in the terms of the
+    paper's Table 2: max over the run of |E - E0| / |E0|, |P - P0| (absolute)
+    and |Lz - Lz0| / |Lz0|, sampled every --drift-every steps (Eq. 8-10 reduced
+    on the GPU in binary64 from the mode's own state)."""
+    import torch
+    import nbody_ics
+    import paper_1803_01190_gb300 as nb
+    w = nbody_ics.workload("disk_halo", n=args.n)
+    out = {"drift": args.drift, "n": args.n, "eps": EPS, "dt": DT, "steps": args.drift_steps,
+           "every": args.drift_every, "workload": workload_desc(args.n)}
+    with nb.Simulation(args.n, mode=args.drift, eps=EPS) as sim:
+        sim.set_state(w["pos"], w["vel"], w["mass"])
+        d0 = sim.diagnostics()
+        curve = []
+        t0 = time.perf_counter()
+        done = 0
+        while done < args.drift_steps:
+            k = min(args.drift_every, args.drift_steps - done)
+            sim.step(DT, k)
+            done += k
+            d = sim.diagnostics()
+            curve.append([done, d["E"] / d0["E"] - 1, float(np.linalg.norm(d["P"] - d0["P"])),
+                          d["L"][2] / d0["L"][2] - 1])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    c = np.array(curve)
+    out.update({"E0": d0["E"], "P0": d0["P"].tolist(), "Lz0": d0["L"][2],
+                "max_dE_over_E0": float(np.abs(c[:, 1]).max()), "max_dP_abs": float(c[:, 2].max()),
+                "max_dLz_over_Lz0": float(np.abs(c[:, 3]).max()), "wall_s": wall,
+                "ms_per_step": wall / args.drift_steps * 1e3, "curve": curve})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,12 +477,18 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--ref-rows", type=int, default=1024)
     ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--drift", choices=["fp64", "f64e", "mixed", "fp32"], default=None,
+                    help="long conservation run of the workload in this mode (Table 2 quantities)")
+    ap.add_argument("--drift-steps", type=int, default=10000)
+    ap.add_argument("--drift-every", type=int, default=100)
     ap.add_argument("--profile-force", choices=["fp64", "f64e", "mixed", "fp32"], default=None,
                     help="run one force evaluation of the workload in this mode and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.profile_force:
+    if args.drift:
+        run_drift(args)
+    elif args.profile_force:
         profile_force(args)
     elif args.impl == "reference":
         run_reference(args)

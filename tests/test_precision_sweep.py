@@ -1,0 +1,59 @@
+"""Precision sweep of the force kernel alone (the benchmark's sweep
+configuration): uniform-in-sphere and Plummer clouds, lognormal masses
+(sigma = 0.5), eps in {1e-3, 1e-2}, in FP64, F64E, MIXED and FP32, with the
+RMS and maximum relative acceleration error against the FP64 oracle on 256
+sampled particles and the force kernel's Ginteractions/s (CUDA events).
+N = 2^16 and 2^18 always; 2^20 and 2^22 when NBODY_SWEEP_LARGE=1 (FP64 and
+F64E only up to 2^20: an FP64 launch at 2^22 takes ten minutes)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import nbody_ics
+import oracle
+from tests.gates import fp64_accel_gate, rel_errors
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+SIZES = [2 ** 16, 2 ** 18] + ([2 ** 20, 2 ** 22] if os.environ.get("NBODY_SWEEP_LARGE") else [])
+
+
+@pytest.fixture(scope="module")
+def nb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_1803_01190_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("dist", ["uniform", "plummer"])
+def test_precision_sweep(nb, n, dist):
+    s = nbody_ics.SEED_BASE + 3
+    pos = (nbody_ics.uniform_sphere(n, s) if dist == "uniform" else nbody_ics.plummer(n, s))[0]
+    mass = nbody_ics.lognormal_masses(n, s + 1)
+    rows = np.sort(np.random.default_rng(n).choice(n, 256, replace=False))
+    for eps in (1e-3, 1e-2):
+        acc_o, _, smag = oracle.accel(pos, mass, eps, rows=rows)
+        for mode in ("fp64", "f64e", "mixed", "fp32"):
+            if mode in ("fp64", "f64e") and n > 2 ** 20:
+                continue
+            with nb.Simulation(n, mode, eps=eps) as sim:
+                sim.profile(True)
+                acc, _ = sim.accel(pos, mass)
+                ms, k = sim.profile_read()
+            e = rel_errors(acc[rows], acc_o)
+            rec = {"dist": dist, "n": n, "eps": eps, "mode": mode, "gint_s": n * n / (ms / k * 1e-3) / 1e9,
+                   "rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max())}
+            print("SWEEP " + json.dumps(rec))
+            if mode in ("fp64", "f64e"):
+                assert fp64_accel_gate(acc[rows], acc_o, smag, n)[0].all(), rec
+            elif mode == "mixed":
+                assert rec["rms"] <= 1e-6, rec
+            else:
+                assert rec["rms"] <= 1e-4, rec
