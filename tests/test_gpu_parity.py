@@ -344,3 +344,41 @@ def test_f64e_kdk_tracks_oracle(nb):
     op, ov, _, _ = oracle.kdk(w["pos"], w["vel"], w["mass"], 0.01, 1.0, 1e-3, 10)
     assert np.abs(p - op).max() <= 1e-12 * np.abs(op).max()
     assert np.abs(v - ov).max() <= 1e-11 * np.abs(ov).max()
+
+
+def test_fp32_kdk_and_diagnostics(nb):
+    """The paper's SP mode keeps its state in binary32: after 10 KDK steps the
+    trajectory stays within float precision of the oracle's, and the Eq. 8-10
+    diagnostics of that state are within float precision of the oracle's."""
+    w = nbody_ics.workload("plummer", n=2048)
+    with nb.Simulation(2048, "fp32", eps=0.01) as sim:
+        sim.set_state(w["pos"], w["vel"], w["mass"])
+        sim.step(1e-3, 10)
+        p, v, t, s = sim.get_state()
+        d = sim.diagnostics()
+        sim.step(1e-3, 2, "rk4")
+        p2, _, _, s2 = sim.get_state()
+    op, ov, _, _ = oracle.kdk(w["pos"], w["vel"], w["mass"], 0.01, 1.0, 1e-3, 10)
+    od = oracle.diag(op, ov, w["mass"], 0.01)
+    assert s == 10 and s2 == 12
+    assert np.abs(p - op).max() <= 1e-5 * np.abs(op).max()
+    assert np.abs(v - ov).max() <= 1e-4 * np.abs(ov).max()
+    assert abs(d["E"] / od["E"] - 1) <= 1e-5
+    assert np.all(p.astype(np.float32).astype(np.float64) == p)      # state is binary32
+    op2, _, _ = oracle.rk4(op, ov, w["mass"], 0.01, 1.0, 1e-3, 2)
+    assert np.abs(p2 - op2).max() <= 1e-5 * np.abs(op2).max()
+
+
+def test_golden_fixture_f64e(nb):
+    from tests.test_oracle_pins import load_golden
+    g = load_golden()
+    n = len(g["mass"])
+    with nb.Simulation(n, "f64e", eps=g["eps"], G=g["G"]) as sim:
+        sim.set_state(g["pos"], g["vel"], g["mass"])
+        acc, pot = sim.get_accel()
+        sim.step(g["dt"], 10, "kdk")
+        kp, kv, _, _ = sim.get_state()
+    _, _, smag = oracle.accel(g["pos"], g["mass"], g["eps"])
+    assert fp64_accel_gate(acc, g["acc"], smag, n)[0].all()
+    assert np.abs(kp - g["kdk_pos"]).max() <= 1e-12 * np.abs(g["pos"]).max()
+    assert np.abs(kv - g["kdk_vel"]).max() <= 1e-12 * np.abs(g["vel"]).max()
