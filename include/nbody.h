@@ -105,6 +105,15 @@ int nbody_set_state(nbody_ctx *ctx, const double *pos, const double *vel, const 
                     int on_device);
 
 /*
+ * Set the model time and step counter reported by nbody_get_state, e.g. after
+ * nbody_set_state from a checkpoint.  Resuming from a checkpoint (set_state
+ * with the saved positions, velocities and masses, then set_clock) continues
+ * the trajectory bit for bit: a(t) is recomputed from the same positions by
+ * the same deterministic kernels.  EINVAL for non-finite t or step < 0.
+ */
+int nbody_set_clock(nbody_ctx *ctx, double t, int64_t step);
+
+/*
  * Read the state at the current step boundary: pos (n x 3), vel (n x 3),
  * the model time *t and the step counter *step.  Any output may be NULL.
  * Synchronises.  ESTATE before nbody_set_state.
@@ -160,7 +169,8 @@ int nbody_diagnostics_ext(nbody_ctx *ctx, double *E, double *K, double *W, doubl
 
 /*
  * Force-kernel launch shape (for tuning; 0 = library default for that field):
- *   ipt    -- i-particles held in registers per thread (1, 2, 4 or 8)
+ *   ipt    -- i-particles held in registers per thread (1, 2, 4 or 8; NBODY_F64E uses
+ *             at most 4)
  *   jsplit -- number of j-segments evaluated by separate thread blocks and
  *             summed afterwards in a fixed order (1..64)
  * The shape changes rounding order only.  EINVAL for unsupported values.

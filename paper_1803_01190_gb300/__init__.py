@@ -129,6 +129,10 @@ class Simulation:
             raise ValueError("pos and mass must both be on the host or both on the device")
         check(lib.nbody_set_state(self._h, pp, pv, pm, dev), "nbody_set_state")
 
+    def set_clock(self, t, step):
+        """Model time and step counter (for resuming from a checkpoint)."""
+        check(lib.nbody_set_clock(self._h, float(t), int(step)), "nbody_set_clock")
+
     def get_state(self, on_device=False):
         """(pos (n,3), vel (n,3), t, step) at the current step boundary."""
         pos, pp = self._out((self.n, 3), on_device)

@@ -35,6 +35,7 @@ _SIGS = {
     "nbody_set_timeout": (_i, [_vp, _d]),
     "nbody_set_state": (_i, [_vp, _vp, _vp, _vp, _i]),
     "nbody_get_state": (_i, [_vp, _vp, _vp, ctypes.POINTER(_d), ctypes.POINTER(_i64), _i]),
+    "nbody_set_clock": (_i, [_vp, _d, _i64]),
     "nbody_accel": (_i, [_vp, _vp, _vp, _vp, _vp, _i]),
     "nbody_get_accel": (_i, [_vp, _vp, _vp, _i]),
     "nbody_step": (_i, [_vp, _i, _d, _i64]),

@@ -13,6 +13,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nbody_internal.cuh"
 
 using nb::d4;
@@ -347,6 +349,14 @@ int nbody_set_state(nbody_ctx *c, const double *pos, const double *vel, const do
   return sync(c);
 }
 
+int nbody_set_clock(nbody_ctx *c, double t, int64_t step) {
+  if (!c) return fail(NBODY_EINVAL, "NULL context");
+  if (!std::isfinite(t) || step < 0) return fail(NBODY_EINVAL, "t must be finite and step >= 0");
+  c->t = t;
+  c->step = step;
+  return NBODY_OK;
+}
+
 int nbody_get_state(nbody_ctx *c, double *pos, double *vel, double *t, int64_t *step,
                     int on_device) {
   if (!c) return fail(NBODY_EINVAL, "NULL context");
@@ -399,10 +409,11 @@ int nbody_accel(nbody_ctx *c, const double *pos, const double *mass, double *acc
         cudaMalloc(&c->tmp_acc, (size_t)c->n * r4(c)) != cudaSuccess)
       return fail(NBODY_ENOMEM, "accel buffers");
   }
+  nvtxRangePushA("nbody_accel");
   int rc = load_arrays(c, pos, nullptr, mass, on_device, c->tmp_posm, nullptr, false);
-  if (rc) return rc;
   int S = 0;
-  rc = force(c, c->tmp_posm, S);
+  if (!rc) rc = force(c, c->tmp_posm, S);
+  nvtxRangePop();
   if (rc) return rc;
   CK(nb::launch_store_acc(c->mode, epi(c, S), c->tmp_acc, c->st));
   c->launches++;
@@ -479,7 +490,10 @@ int nbody_step(nbody_ctx *c, int scheme, double dt, int64_t nsteps) {
   if (nsteps < 0) return fail(NBODY_EINVAL, "nsteps < 0");
   if (!c->has_state) return fail(NBODY_ESTATE, "step before set_state");
   CK(cudaSetDevice(c->device));
-  return scheme == NBODY_KDK ? step_kdk(c, dt, nsteps) : step_rk4(c, dt, nsteps);
+  nvtxRangePushA(scheme == NBODY_KDK ? "nbody_step KDK" : "nbody_step RK4");
+  const int rc = scheme == NBODY_KDK ? step_kdk(c, dt, nsteps) : step_rk4(c, dt, nsteps);
+  nvtxRangePop();
+  return rc;
 }
 
 int nbody_diagnostics_ext(nbody_ctx *c, double *E, double *K, double *W, double *P, double *L) {

@@ -30,6 +30,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nbody_internal.cuh"
 
 using nb::d4;
@@ -538,9 +540,18 @@ int nbody_batch_evict(nbody_batch *b, int slot) {
   return NBODY_OK;
 }
 
+static int batch_step_impl(nbody_batch *b, int64_t nticks);
+
 int nbody_batch_step(nbody_batch *b, int64_t nticks) {
   if (!b || nticks < 0) return bfail(NBODY_EINVAL, "batch step");
   BCK(cudaSetDevice(b->device));
+  nvtxRangePushA("nbody_batch_step");
+  const int rc = batch_step_impl(b, nticks);
+  nvtxRangePop();
+  return rc;
+}
+
+static int batch_step_impl(nbody_batch *b, int64_t nticks) {
   for (int64_t t = 0; t < nticks; t++) {
     if (b->dirty) {
       int rc = build_tables(b);
