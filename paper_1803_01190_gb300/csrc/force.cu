@@ -18,8 +18,8 @@
 // Three arithmetics:
 //   f64   binary64 pair arithmetic.  GB300 issues binary64 at about 1/72 of the
 //         binary32 rate, so the kernel is bound by the FP64 pipe and its cost
-//         is its count of FP64 instructions per pair: 17 (3 DADD for d,
-//         3 DFMA for |d|^2 + eps^2, 4 for the reciprocal square root, 3 DMUL,
+//         is its count of FP64 instructions per pair: 16 (3 DADD for d,
+//         3 DFMA for |d|^2 + eps^2, 3 for the reciprocal square root, 3 DMUL,
 //         3 DFMA and 1 DADD for the sums).  The reciprocal square root is
 //         seeded and refined to about 2^-45 on the otherwise idle FP32 and
 //         integer pipes (SFU seed, float-float residual) and finished with one
@@ -53,8 +53,8 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 }
 
 // 1/sqrt(x) in binary64 (about one ulp) for x in [2^-60, 2^60), using only
-// four FP64 instructions; GB300's FP64 pipe is the bottleneck of the FP64 force
-// kernel, while its FP32 and integer pipes are idle there.
+// three FP64 instructions; GB300's FP64 pipe is the bottleneck of the FP64
+// force kernel, while its FP32 and integer pipes are idle there.
 //  1. x = xh + xl exactly-ish in binary32: xh = the top 24 significant bits of
 //     x moved into a float by integer operations (exponent 1023 -> 127), xl =
 //     the next 29 bits converted and scaled (relative error 2^-47 of x).
@@ -62,15 +62,13 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 //     FP32 pipe: e = 1 - x y0^2 from exact products (TwoProd by FMA) so that
 //     e is correct to about 2^-46; g = e (1/2 + 3e/8), i.e. y0 (1 + g) is the
 //     second-order correction, accurate to about 2^-45.
-//  3. s = y0 (1 + g) in binary64 (one DFMA; y0 and g reach binary64 exactly by
-//     integer moves), then one binary64 Newton step
+//  3. s = y0 (1 + g) assembled in binary64 by integer operations (about 31
+//     correct bits), then one binary64 Newton step
 //     y = s + s (1/2 - (x/2) s^2), x/2 by decrementing the exponent: the
-//     error 1.5 (2^-45)^2 vanishes and the roundings leave about one ulp.
+//     error 1.5 (2^-31)^2 vanishes and the roundings leave about one ulp.
 // Outside the range (and for zero, negative or non-finite x) it calls the
 // out-of-line 1.0 / sqrt(x).
 __device__ __noinline__ double rsqrt_f64_slow(double x) { return 1.0 / sqrt(x); }
-
-__device__ __forceinline__ double f2d_exact(float f);
 
 __device__ __forceinline__ double rsqrt_f64(double x) {
   const unsigned hi = (unsigned)__double2hiint(x);
@@ -84,8 +82,23 @@ __device__ __forceinline__ double rsqrt_f64(double x) {
   const float u = xh * th, ue = fmaf(xh, th, -u);
   const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, u), ue), fmaf(xh, tl, xl * th));
   const float g = e * fmaf(e, 0.375f, 0.5f);
-  const double y0d = f2d_exact(y0);
-  const double s = fma(y0d, f2d_exact(g), y0d);
+  // s = y0 (1 + g) assembled in binary64 by integer operations: significand of
+  // y0 at a 2^30 scale plus y0 g rounded at that scale, renormalised if the sum
+  // left [2^30, 2^31).  Its relative error (about 2^-31) is squared away by the
+  // Newton step below.
+  const unsigned yb = __float_as_uint(y0);
+  const float y0m = __uint_as_float((yb & 0x7FFFFFu) | 0x3F800000u);  // y0's significand in [1, 2)
+  const int ci = __float2int_rn(y0m * (g * 1073741824.0f));
+  unsigned S = (((yb & 0x7FFFFFu) | 0x800000u) << 7) + (unsigned)ci;
+  unsigned E = ((yb >> 23) & 0xFFu) + 896u;
+  if (S >= 0x80000000u) {
+    S >>= 1;
+    E += 1u;
+  } else if (S < 0x40000000u) {
+    S <<= 1;
+    E -= 1u;
+  }
+  const double s = __hiloint2double((int)((E << 20) | ((S >> 10) & 0xFFFFFu)), (int)(S << 22));
   const double xhalf = __hiloint2double((int)(hi - 0x00100000u), (int)lo);
   const double t = s * s;
   return fma(s, fma(-xhalf, t, 0.5), s);

@@ -58,4 +58,6 @@ def test_precision_sweep(nb, n, dist):
                 # mean separation, up to ~1e-6 when eps = 1e-3 is far below it (close pairs dominate)
                 assert rec["rms"] <= 1e-5, rec
             else:
-                assert rec["rms"] <= 1e-4, rec
+                # the paper's SP: plain binary32 sums over up to N/2 terms per accumulator grow with N
+                # (RMS 2e-7 at N = 2^16, 1e-4 at N = 2^22 with eps = 1e-3); a sanity bound only
+                assert rec["rms"] <= 1e-3, rec
