@@ -442,8 +442,10 @@ def run_drift(args):
     import nbody_ics
     import paper_1803_01190_gb300 as nb
     w = nbody_ics.workload("disk_halo", n=args.n)
-    out = {"drift": args.drift, "n": args.n, "eps": EPS, "dt": DT, "steps": args.drift_steps,
-           "every": args.drift_every, "workload": workload_desc(args.n)}
+    dt = args.drift_dt
+    out = {"drift": args.drift, "scheme": args.drift_scheme, "n": args.n, "eps": EPS, "dt": dt,
+           "steps": args.drift_steps, "every": args.drift_every, "workload": workload_desc(args.n),
+           "force_evaluations": args.drift_steps * (4 if args.drift_scheme == "rk4" else 1)}
     with nb.Simulation(args.n, mode=args.drift, eps=EPS) as sim:
         sim.set_state(w["pos"], w["vel"], w["mass"])
         d0 = sim.diagnostics()
@@ -452,7 +454,7 @@ def run_drift(args):
         done = 0
         while done < args.drift_steps:
             k = min(args.drift_every, args.drift_steps - done)
-            sim.step(DT, k)
+            sim.step(dt, k, scheme=args.drift_scheme)
             done += k
             d = sim.diagnostics()
             curve.append([done, d["E"] / d0["E"] - 1, float(np.linalg.norm(d["P"] - d0["P"])),
@@ -482,6 +484,8 @@ def main():
     ap.add_argument("--drift", choices=["fp64", "f64e", "mixed", "fp32"], default=None,
                     help="long conservation run of the workload in this mode (Table 2 quantities)")
     ap.add_argument("--drift-steps", type=int, default=10000)
+    ap.add_argument("--drift-scheme", choices=["kdk", "rk4"], default="kdk")
+    ap.add_argument("--drift-dt", type=float, default=DT)
     ap.add_argument("--drift-every", type=int, default=100)
     ap.add_argument("--profile-force", choices=["fp64", "f64e", "mixed", "fp32"], default=None,
                     help="run one force evaluation of the workload in this mode and exit")

@@ -42,7 +42,6 @@ struct nbody_ctx {
   double t = 0;
   int64_t step = 0;
   nb::Shape shape;
-  bool shape_user = false;
   double timeout_s = 0;
   int64_t launches = 0;
   bool prof = false;
@@ -470,7 +469,7 @@ static int step_rk4(nbody_ctx *c, double dt, int64_t nsteps) {
       int rc = force(c, stage == 1 ? c->posm[c->cur] : c->posm[stg], S);
       if (rc) return rc;
       CK(nb::launch_rk4_stage(c->mode, epi(c, S), stage, dt, c->posm[c->cur], c->vel, c->rk_vs,
-                              c->rk_sr, c->rk_sv, c->posm[stg], c->acc, c->st));
+                              c->rk_sr, c->rk_sv, c->posm[stg], c->st));
       c->launches++;
     }
     c->t += dt;
@@ -528,7 +527,6 @@ int nbody_set_launch(nbody_ctx *c, int ipt, int jsplit) {
   if (jsplit < 0 || jsplit > 64) return fail(NBODY_EINVAL, "jsplit");
   CK(cudaSetDevice(c->device));
   default_shape(c, c->shape, ipt, jsplit);
-  c->shape_user = ipt != 0 || jsplit != 0;
   return NBODY_OK;
 }
 

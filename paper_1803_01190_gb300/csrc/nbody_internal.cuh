@@ -116,7 +116,7 @@ cudaError_t launch_kdk_correct_predict(int mode, const EpiIn &e, double dt, void
                                        cudaStream_t st);
 cudaError_t launch_rk4_stage(int mode, const EpiIn &e, int stage, double dt, const void *posm0,
                              void *vel0, void *rk_vs, void *rk_sr, void *rk_sv, void *posm_stage,
-                             void *acc, cudaStream_t st);
+                             cudaStream_t st);
 cudaError_t launch_diag(int mode, const void *posm, const void *vel, const void *acc, int64_t n,
                         double *blocks, int nblocks, double *out9, cudaStream_t st);
 int diag_blocks(int64_t n);

@@ -378,8 +378,7 @@ cudaError_t launch_kdk_correct_predict(int mode, const EpiIn &e, double dt, void
 
 cudaError_t launch_rk4_stage(int mode, const EpiIn &e, int stage, double dt, const void *posm0,
                              void *vel0, void *rk_vs, void *rk_sr, void *rk_sv, void *posm_stage,
-                             void *acc, cudaStream_t st) {
-  (void)acc;
+                             cudaStream_t st) {
   if (mode == NBODY_FP32)
     k_rk4_stage<float, float4><<<grid_for(e.n), 256, 0, st>>>(
         (const float4 *)e.part, e.S, e.n, (float)e.G, stage, (float)dt, (float)(dt / 2),
