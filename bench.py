@@ -414,6 +414,11 @@ def run_gpu(args):
                                    "mixed": drift(mixed["diag0"], mixed["diags"])},
         "serving": serving,
         "serving_fp64_requests_on_f64e": serving_f64e,
+        "paper_context": {
+            "note": "the paper's Table 1, one Tesla K80, its own disk model (not this workload): "
+                    "seconds per KDK step at N = 1024K, as N^2 interactions per second",
+            "dp_k80_ginteractions_per_s": 1048576.0 ** 2 / 60.0 / 1e9,
+            "sp_k80_ginteractions_per_s": 1048576.0 ** 2 / 27.4 / 1e9},
     }
     print(json.dumps(line), flush=True)
     if world > 1:
