@@ -65,7 +65,8 @@ def _kernel_src_sha(names):
 
 def traffic_f64(n):
     t = TRAFFIC["k_force_f64"]
-    sha = _kernel_src_sha(["__device__ __forceinline__ double rsqrt_f64(",
+    sha = _kernel_src_sha(["__device__ __forceinline__ void rsqrt_recip_sig(",
+                           "__device__ __forceinline__ uint64_t mul_sig(",
                            "__device__ __forceinline__ void body_f64(",
                            "__global__ void __launch_bounds__(BT) k_force_f64("])
     return t["bytes"] if (sha == t["src_sha"] and n == t["n"]) else None

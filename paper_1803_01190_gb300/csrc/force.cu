@@ -18,12 +18,12 @@
 // Three arithmetics:
 //   f64   binary64 pair arithmetic.  GB300 issues binary64 at about 1/72 of the
 //         binary32 rate, so the kernel is bound by the FP64 pipe and its cost
-//         is its count of FP64 instructions per pair: 16 (3 DADD for d,
-//         3 DFMA for |d|^2 + eps^2, 3 for the reciprocal square root, 3 DMUL,
-//         3 DFMA and 1 DADD for the sums).  The reciprocal square root is
-//         seeded and refined to about 2^-45 on the otherwise idle FP32 and
-//         integer pipes (SFU seed, float-float residual) and finished with one
-//         binary64 Newton step.
+//         is its count of FP64 instructions per pair: 10 (3 DADD for d,
+//         3 DFMA for |d|^2 + eps^2, 3 DFMA and 1 DADD for the sums).  The
+//         rest runs on the otherwise idle integer and FP32 pipes: 1/r and
+//         1/r^2 within 0.52 ulp (SFU seed, exact integer residual) and the
+//         products m/r and (m/r)/r^2 by a correctly rounded integer binary64
+//         multiply.
 //   mixed binary32 pair arithmetic (packed: two j per instruction, SFU
 //         reciprocal square root) on coordinates
 //         re-centred on an anchor (the per-coordinate median) per j-tile, with the i coordinates held as float-float pairs so that the
@@ -52,56 +52,110 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return y;
 }
 
-// 1/sqrt(x) in binary64 (about one ulp) for x in [2^-60, 2^60), using only
-// three FP64 instructions; GB300's FP64 pipe is the bottleneck of the FP64
-// force kernel, while its FP32 and integer pipes are idle there.
-//  1. x = xh + xl exactly-ish in binary32: xh = the top 24 significant bits of
-//     x moved into a float by integer operations (exponent 1023 -> 127), xl =
-//     the next 29 bits converted and scaled (relative error 2^-47 of x).
+// 1/sqrt(x) and 1/x in binary64 (each within about 0.52 ulp) for x in
+// [2^-60, 2^60), without any FP64 instruction: GB300's FP64 pipe is the
+// bottleneck of the FP64 force kernel, while its FP32 and integer pipes are
+// idle there.  Inputs are the two halves of x; outputs are the 53-bit
+// significands (in [2^52, 2^53)) and biased binary64 exponents.
+//  1. x = xh + xl in binary32: xh = the top 24 significant bits of x moved
+//     into a float by integer operations (exponent 1023 -> 127), xl = the
+//     next 29 bits converted and scaled (relative error 2^-47 of x).
 //  2. Seed y0 = SFU rsqrt(xh) (relative error below 2^-21), improved on the
-//     FP32 pipe: e = 1 - x y0^2 from exact products (TwoProd by FMA) so that
-//     e is correct to about 2^-46; g = e (1/2 + 3e/8), i.e. y0 (1 + g) is the
-//     second-order correction, accurate to about 2^-45.
-//  3. s = y0 (1 + g) assembled in binary64 by integer operations (about 31
-//     correct bits), then one binary64 Newton step
-//     y = s + s (1/2 - (x/2) s^2), x/2 by decrementing the exponent: the
-//     error 1.5 (2^-31)^2 vanishes and the roundings leave about one ulp.
-// Outside the range (and for zero, negative or non-finite x) it calls the
-// out-of-line 1.0 / sqrt(x).
-__device__ __noinline__ double rsqrt_f64_slow(double x) { return 1.0 / sqrt(x); }
-
-__device__ __forceinline__ double rsqrt_f64(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x);
-  if (hi - 0x3C300000u >= 0x43B00000u - 0x3C300000u) return rsqrt_f64_slow(x);
-  const unsigned lo = (unsigned)__double2loint(x);
+//     FP32 pipe: e0 = 1 - x y0^2 from exact products (TwoProd by FMA);
+//     g = e0 (1/2 + 3 e0/8), the second-order correction.
+//  3. s = y0 (1 + g) as an integer significand S in [2^30, 2^31) with a
+//     binary64 exponent E: s = S 2^(E - 1053), |x s^2 - 1| < 2^-29.
+//  4. Exact residual in integers: with X the 53-bit significand of x,
+//     P = X S^2 is within 2^(K-29) of 2^K, K = 3181 - Ex - 2E; the low 96 bits
+//     of P (three 32x32 products and the high half of the fourth) give
+//     T = (P - 2^K) / 2^32 exactly as a signed 64-bit integer, and
+//     e = 1 - x s^2 = -T 2^(32-K).
+//  5. 1/sqrt(x) = s (1 + e/2 + 3e^2/8 + ...) and 1/x = s^2 (1 + e + e^2 ...);
+//     e^2 < 2^-58 is below the rounding, so the significands are
+//     S 2^22 - S T 2^(53-K) and S^2 / 2^sh - (S^2 / 2^32) T 2^(64-K-sh), formed
+//     with 8 fraction bits, renormalised by one bit if they left [2^52, 2^53)
+//     and rounded to nearest.
+__device__ __forceinline__ void rsqrt_recip_sig(unsigned hi, unsigned lo, uint64_t &R, int &ER,
+                                                uint64_t &Q, int &EQ) {
+  // 1-2: binary32 seed and second-order correction
   const float xh = __uint_as_float(__funnelshift_l(lo, hi - 0x38000000u, 3));
-  const float scale = __uint_as_float(((hi >> 20) - 948u) << 23);  // 2^(E - 1075)
+  const float scale = __uint_as_float(((hi >> 20) - 948u) << 23);  // 2^(Ex - 1075)
   const float xl = __uint2float_rn(lo & 0x1FFFFFFFu) * scale;
   const float y0 = rsqrt_approx(xh);
   const float th = y0 * y0, tl = fmaf(y0, y0, -th);
   const float u = xh * th, ue = fmaf(xh, th, -u);
-  const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, u), ue), fmaf(xh, tl, xl * th));
-  const float g = e * fmaf(e, 0.375f, 0.5f);
-  // s = y0 (1 + g) assembled in binary64 by integer operations: significand of
-  // y0 at a 2^30 scale plus y0 g rounded at that scale, renormalised if the sum
-  // left [2^30, 2^31).  Its relative error (about 2^-31) is squared away by the
-  // Newton step below.
+  const float e0 = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, u), ue), fmaf(xh, tl, xl * th));
+  const float g = e0 * fmaf(e0, 0.375f, 0.5f);
+  // 3: S = y0's significand at a 2^30 scale plus y0 g rounded at that scale
   const unsigned yb = __float_as_uint(y0);
   const float y0m = __uint_as_float((yb & 0x7FFFFFu) | 0x3F800000u);  // y0's significand in [1, 2)
   const int ci = __float2int_rn(y0m * (g * 1073741824.0f));
   unsigned S = (((yb & 0x7FFFFFu) | 0x800000u) << 7) + (unsigned)ci;
-  unsigned E = ((yb >> 23) & 0xFFu) + 896u;
+  int E = (int)((yb >> 23) & 0xFFu) + 896;
   if (S >= 0x80000000u) {
     S >>= 1;
-    E += 1u;
+    E += 1;
   } else if (S < 0x40000000u) {
     S <<= 1;
-    E -= 1u;
+    E -= 1;
   }
-  const double s = __hiloint2double((int)((E << 20) | ((S >> 10) & 0xFFFFFu)), (int)(S << 22));
-  const double xhalf = __hiloint2double((int)(hi - 0x00100000u), (int)lo);
-  const double t = s * s;
-  return fma(s, fma(-xhalf, t, 0.5), s);
+  // 4: T = (X S^2 - 2^K) / 2^32 from the low 96 bits of the product
+  const int Ex = (int)(hi >> 20);
+  const unsigned a1 = (hi & 0xFFFFFu) | 0x100000u;
+  const uint64_t S2 = (uint64_t)S * S;
+  const unsigned b1 = (unsigned)(S2 >> 32), b0 = (unsigned)S2;
+  uint64_t Tu = (uint64_t)a1 * b0 + __umulhi(lo, b0);
+  Tu += (uint64_t)lo * b1;
+  Tu += (uint64_t)(a1 * b1) << 32;
+  const int Th = (int)(Tu >> 32);
+  const unsigned Tl = (unsigned)Tu;
+  // 5a: 1/sqrt(x)
+  const int64_t ST = (int64_t)(int)S * Th + (int64_t)__umulhi(S, Tl);  // S T / 2^32
+  const int64_t Rf = (int64_t)((uint64_t)S << 30) - (ST >> (3088 - Ex - 2 * E));
+  const int sR = 8 + (Rf >= (int64_t)1 << 61) - (Rf < (int64_t)1 << 60);
+  R = (uint64_t)(Rf + ((int64_t)1 << (sR - 1))) >> sR;
+  ER = E + sR - 8;
+  // 5b: 1/x
+  const int sh = 8 + (b1 >= 0x20000000u);
+  const int64_t BT = (int64_t)b1 * Th + (int64_t)__umulhi(b1, Tl);  // (S^2 / 2^32) T / 2^32
+  const int64_t Qf = (int64_t)(S2 >> (sh - 8)) - (BT >> (3077 - Ex - 2 * E + sh));
+  const int sQ = 8 + (Qf >= (int64_t)1 << 61) - (Qf < (int64_t)1 << 60);
+  Q = (uint64_t)(Qf + ((int64_t)1 << (sQ - 1))) >> sQ;
+  EQ = sh + 2 * E - 1031 + sQ - 8;
+}
+
+// Binary64 multiplication on the integer pipes, correctly rounded (to nearest,
+// ties to even): significands A in [2^52, 2^53] and B in [2^52, 2^53) with
+// biased exponents ea, eb; the caller guarantees a normal result.  The 106-bit
+// product comes from four 32x32 products; U = its top 64 bits (in [2^62, 2^64)),
+// the bits below form the sticky bit.  Returns the significand (2^53 after a
+// rounding carry, which the packing below absorbs into the exponent) and the
+// biased exponent.
+__device__ __forceinline__ uint64_t mul_sig(uint64_t A, int ea, uint64_t B, int eb, int &e) {
+  const unsigned a1 = (unsigned)(A >> 32), a0 = (unsigned)A;
+  const unsigned b1 = (unsigned)(B >> 32), b0 = (unsigned)B;
+  const uint64_t lo = (uint64_t)a0 * b0;
+  uint64_t V = (uint64_t)a1 * b0 + (lo >> 32);
+  V += (uint64_t)a0 * b1;
+  const uint64_t U = (((uint64_t)a1 * b1) << 22) + (V >> 10);
+  const int n = (int)(U >> 63);
+  const int sft = 10 + n;
+  const uint64_t sig = U >> sft;
+  const uint64_t rb = (U >> (sft - 1)) & 1u;
+  const bool st = ((U & (((uint64_t)1 << (sft - 1)) - 1u)) | (V & 0x3FFu) | (unsigned)lo) != 0;
+  e = ea + eb - 1023 + n;
+  return sig + (rb & (uint64_t)(st | (bool)(sig & 1u)));
+}
+__device__ __forceinline__ double pack_f64(uint64_t sig, int e) {
+  return __longlong_as_double((long long)((((uint64_t)(e - 1)) << 52) + sig));
+}
+
+// The same quantities in binary64 arithmetic, out of line: for r^2 outside
+// [2^-60, 2^60) (and zero or non-finite) and for masses outside
+// [2^-895, 2^897) (and zero), where the integer path's ranges do not hold.
+__device__ __noinline__ double2 pair_scale_f64_slow(double r2, double m) {
+  const double my = m * (1.0 / sqrt(r2));
+  return make_double2(my, my * (1.0 / r2));
 }
 
 // float-float accumulation a += b (Knuth's TwoSum; exact error term).
@@ -159,9 +213,24 @@ __device__ __forceinline__ void body_f64(const d4 &pj, double xi, double yi, dou
     r2 = 1.0;
     m = 0.0;
   }
-  const double y = rsqrt_f64(r2);
-  const double my = m * y;
-  const double f = my * (y * y);
+  // my = m / r and f = my / r^2, both binary64 products correctly rounded
+  const unsigned hi = (unsigned)__double2hiint(r2);
+  const unsigned mh = (unsigned)__double2hiint(m);
+  double my, f;
+  if (hi - 0x3C300000u < 0x43B00000u - 0x3C300000u && (mh >> 20) - 128u < 1793u) {
+    uint64_t R, Q;
+    int ER, EQ, emy, ef;
+    rsqrt_recip_sig(hi, (unsigned)__double2loint(r2), R, ER, Q, EQ);
+    const uint64_t Am = ((uint64_t)((mh & 0xFFFFFu) | 0x100000u) << 32) | (unsigned)__double2loint(m);
+    const uint64_t smy = mul_sig(Am, (int)(mh >> 20), R, ER, emy);
+    const uint64_t sf = mul_sig(smy, emy, Q, EQ, ef);
+    my = pack_f64(smy, emy);
+    f = pack_f64(sf, ef);
+  } else {
+    const double2 v = pair_scale_f64_slow(r2, m);
+    my = v.x;
+    f = v.y;
+  }
   ax = fma(dx, f, ax);
   ay = fma(dy, f, ay);
   az = fma(dz, f, az);
