@@ -3,9 +3,9 @@
 Only the tests, the smoke check and the benchmark's CPU-baseline leg may
 import this package; the GPU library never does, and this package never
 imports the GPU library.  It wraps the plain C oracle in nbody_oracle.c
-(Eq. 1-2 force and potential, Eq. 5-7 KDK leapfrog, classical RK4 as the
-reading of the paper's fourth-order scheme, Eq. 8-10 diagnostics) with numpy
-arrays.  Arrays are float64, C-contiguous, positions/velocities shaped (n, 3).
+(Eq. 1-2 force and potential, Eq. 5-7 KDK leapfrog, classical RK4 and the
+fourth-order symplectic composition of the KDK step as the two readings of
+the paper's fourth-order scheme, Eq. 8-10 diagnostics) with numpy arrays.  Arrays are float64, C-contiguous, positions/velocities shaped (n, 3).
 """
 import ctypes
 import os
@@ -38,11 +38,13 @@ class Oracle:
                                      ctypes.c_int64, _ip, _dp, _dp, _dp, ctypes.c_int]
         lib.oracle_kdk.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_int64, _dp, _dp, ctypes.c_int]
+        lib.oracle_fr4.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int64, _dp, _dp, ctypes.c_int]
         lib.oracle_rk4.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_int64, _dp, ctypes.c_int]
         lib.oracle_diag.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                     _dp, ctypes.c_int]
-        for f in (lib.oracle_accel, lib.oracle_kdk, lib.oracle_rk4, lib.oracle_diag):
+        for f in (lib.oracle_accel, lib.oracle_kdk, lib.oracle_fr4, lib.oracle_rk4, lib.oracle_diag):
             f.restype = ctypes.c_int
         lib.oracle_max_threads.restype = ctypes.c_int
         self.lib = lib
@@ -88,6 +90,25 @@ class Oracle:
                                  int(nsteps), _d(acc), _d(pot), int(threads))
         if rc != 0:
             raise ValueError("oracle_kdk: bad argument")
+        return pos, vel, acc, pot
+
+    def fr4(self, pos, vel, mass, eps, G, dt, nsteps, acc0=None, threads=0):
+        """Fourth-order symplectic composition of Eq. 5-7 (three KDK steps of
+        w1 dt, w0 dt, w1 dt).  Returns (pos, vel, acc, pot) at the end;
+        acc0 = a(t0) (evaluated here when None)."""
+        pos = _f64(pos, (-1, 3)).copy()
+        vel = _f64(vel, (-1, 3)).copy()
+        mass = _f64(mass, (-1,))
+        n = pos.shape[0]
+        if acc0 is None:
+            acc = self.accel(pos, mass, eps, G, threads=threads)[0]
+        else:
+            acc = _f64(acc0, (-1, 3)).copy()
+        pot = np.empty(n)
+        rc = self.lib.oracle_fr4(n, _d(pos), _d(vel), _d(mass), float(eps), float(G), float(dt),
+                                 int(nsteps), _d(acc), _d(pot), int(threads))
+        if rc != 0:
+            raise ValueError("oracle_fr4: bad argument")
         return pos, vel, acc, pot
 
     def rk4(self, pos, vel, mass, eps, G, dt, nsteps, threads=0):
@@ -137,6 +158,10 @@ def accel(*a, **k):
 
 def kdk(*a, **k):
     return default().kdk(*a, **k)
+
+
+def fr4(*a, **k):
+    return default().fr4(*a, **k)
 
 
 def rk4(*a, **k):

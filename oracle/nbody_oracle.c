@@ -19,6 +19,9 @@
  *   oracle_rk4    -- the fourth-order scheme of the abstract, read as the
  *                    classical Runge-Kutta method on (r, v) (the paper does not
  *                    define its fourth-order scheme).
+ *   oracle_fr4    -- the other reading of that scheme: the fourth-order
+ *                    symplectic composition of the KDK step of Eq. 5-7
+ *                    (Yoshida 1990; Forest and Ruth 1990).
  *   oracle_diag   -- Eq. 8-10 (section 3): E, P, L (full vector; L_z is Eq. 10).
  *                    Eq. 8 prints the potential term with a + sign; a bound
  *                    self-gravitating system has negative potential energy, so
@@ -211,6 +214,35 @@ int oracle_rk4(int64_t n, double *pos, double *vel, const double *mass,
     }
     oracle_accel(n, pos, mass, eps, G, 0, NULL, acc, NULL, NULL, nthreads);
     free(a1); free(a2); free(a3); free(a4); free(v2); free(v3); free(v4); free(rs);
+    return 0;
+}
+
+/*
+ * Fourth-order symplectic composition of the KDK step (H. Yoshida, 1990,
+ * "Construction of higher order symplectic integrators", Phys. Lett. A 150,
+ * 262; E. Forest and R. D. Ruth, 1990, Physica D 43, 105): one step of size
+ * dt is three steps of Eq. 5-7 of sizes w1 dt, w0 dt, w1 dt, with
+ *   w1 = 1 / (2 - 2^(1/3)),   w0 = -2^(1/3) / (2 - 2^(1/3)),
+ * so that 2 w1 + w0 = 1 (consistency) and 2 w1^3 + w0^3 = 0, which cancels
+ * the third-order error term of the time-symmetric KDK step.  The middle step
+ * runs backwards in time.  Three force evaluations per step: the force at the
+ * end of one KDK step is the start of the next.  acc holds a(t0) on entry and
+ * a at the final positions on return; pot (may be NULL) the potential there.
+ * The weights are the binary64 roundings of the exact values.
+ */
+#define FR4_W1 0x1.59e8b6eb96338p+0  /* 1.3512071919596576... */
+#define FR4_W0 -0x1.b3d16dd72c671p+0 /* -1.7024143839193153... */
+int oracle_fr4(int64_t n, double *pos, double *vel, const double *mass,
+               double eps, double G, double dt, int64_t nsteps,
+               double *acc, double *pot, int nthreads) {
+    if (n < 1 || !pos || !vel || !mass || !acc || nsteps < 0) return -1;
+    const double w[3] = {FR4_W1, FR4_W0, FR4_W1};
+    if (nsteps == 0) return oracle_kdk(n, pos, vel, mass, eps, G, dt, 0, acc, pot, nthreads);
+    for (int64_t st = 0; st < nsteps; st++)
+        for (int s = 0; s < 3; s++) {
+            double *p = (st == nsteps - 1 && s == 2) ? pot : NULL;
+            if (oracle_kdk(n, pos, vel, mass, eps, G, w[s] * dt, 1, acc, p, nthreads)) return -1;
+        }
     return 0;
 }
 

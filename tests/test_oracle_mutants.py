@@ -30,6 +30,11 @@ MUTANTS = {
     "rk4_weight": ("pos[k] = pos[k] + (dt / 6) * (vel[k] + 2 * v2[k] + 2 * v3[k] + v4[k]);",
                    "pos[k] = pos[k] + (dt / 6) * (vel[k] + 2 * v2[k] + v3[k] + 2 * v4[k]);"),
     "rk4_stage3_from_stage1": ("rs[k] = pos[k] + dt * v3[k];", "rs[k] = pos[k] + dt * v2[k];"),
+    "fr4_asymmetric": ("const double w[3] = {FR4_W1, FR4_W0, FR4_W1};",
+                       "const double w[3] = {FR4_W0, FR4_W1, FR4_W1};"),
+    "fr4_w0_one_minus_w1": ("#define FR4_W0 -0x1.b3d16dd72c671p+0", "#define FR4_W0 (1 - FR4_W1)"),
+    "fr4_weights_dropped": ("oracle_kdk(n, pos, vel, mass, eps, G, w[s] * dt, 1, acc, p, nthreads)",
+                            "oracle_kdk(n, pos, vel, mass, eps, G, dt, 1, acc, p, nthreads)"),
     "diag_W_sign": ("nsum_add(&W, m * pot[i] / 2);", "nsum_add(&W, -m * pot[i] / 2);"),
     "diag_W_not_halved": ("nsum_add(&W, m * pot[i] / 2);", "nsum_add(&W, m * pot[i]);"),
     "diag_Lz_transposed": ("nsum_add(&L[2], m * (r[0] * v[1] - r[1] * v[0]));",
@@ -49,6 +54,8 @@ PINS = [
     (pins.test_kdk_energy_bounded_and_second_order, {}),
     (pins.test_kdk_time_reversible, {}),
     (pins.test_rk4_fourth_order_on_kepler_orbit, {}),
+    (pins.test_fr4_fourth_order_on_kepler_orbit, {}),
+    (pins.test_fr4_time_reversible, {}),
     (pins.test_diag_two_body_circular, {}),
     (pins.test_diag_three_bodies_by_hand, {}),
 ]

@@ -232,6 +232,53 @@ def test_rk4_fourth_order_on_kepler_orbit(oracle):
     assert errs[-1] < 1e-6
 
 
+# ---------------------------------------------------------------- FR4 (KDK composition)
+def test_fr4_fourth_order_on_kepler_orbit(oracle):
+    """Against Kepler's equation after one orbit of e = 0.5: the error falls by
+    ~16 per halving of dt (fourth order)."""
+    pos, vel, mass = kepler.two_body(0.0, e=0.5)
+    T = kepler.period()
+    pw, _, _ = kepler.two_body(T, e=0.5)
+    errs = []
+    for spo in (200, 400, 800):
+        p, v, _, _ = oracle.fr4(pos, vel, mass, 0.0, 1.0, T / spo, spo)
+        errs.append(np.abs(p - pw).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 13 < r1 < 19 and 13 < r2 < 19, (errs, r1, r2)
+    assert errs[-1] < 1e-5
+
+
+def test_fr4_energy_bounded_and_fourth_order(oracle):
+    """The composition is symplectic: the energy error of an e = 0.3 Kepler
+    orbit, sampled 32 times per orbit over 5 orbits, shows no secular growth,
+    and its maximum scales as dt^4."""
+    pos, vel, mass = kepler.two_body(0.0, e=0.3)
+    E0 = oracle.diag(pos, vel, mass, 0.0)["E"]
+    T = kepler.period()
+    maxerr = []
+    for spo in (128, 256):
+        p, v = pos, vel
+        errs = []
+        for _ in range(5 * 32):
+            p, v, _, _ = oracle.fr4(p, v, mass, 0.0, 1.0, T / spo, spo // 32)
+            errs.append(abs(oracle.diag(p, v, mass, 0.0)["E"] / E0 - 1))
+        errs = np.array(errs)
+        assert errs[-32:].max() < 1.05 * errs[:32].max()
+        maxerr.append(errs.max())
+    assert 12 < maxerr[0] / maxerr[1] < 20, maxerr
+
+
+def test_fr4_time_reversible(oracle):
+    """n steps forward, reverse velocities, n steps, reverse again: back to
+    the start to round-off (the composition is time symmetric)."""
+    w = nbody_ics.workload("plummer", n=64)
+    p, v, m = w["pos"], w["vel"], w["mass"]
+    p1, v1, _, _ = oracle.fr4(p, v, m, 0.05, 1.0, 1e-3, 20)
+    p2, v2, _, _ = oracle.fr4(p1, -v1, m, 0.05, 1.0, 1e-3, 20)
+    assert np.abs(p2 - p).max() < 1e-12
+    assert np.abs(-v2 - v).max() < 1e-11
+
+
 # ---------------------------------------------------------------- diagnostics, Eq. 8-10
 def test_diag_two_body_circular(oracle):
     """m = 1/2 each, separation 1, circular: E = -G m1 m2 / (2 d) = -1/8,
@@ -273,6 +320,7 @@ def load_golden():
     t = np.loadtxt(path)
     return dict(pos=t[:, 0:3], vel=t[:, 3:6], mass=t[:, 6], acc=t[:, 7:10], pot=t[:, 10],
                 kdk_pos=t[:, 11:14], kdk_vel=t[:, 14:17], rk4_pos=t[:, 17:20], rk4_vel=t[:, 20:23],
+                fr4_pos=t[:, 23:26], fr4_vel=t[:, 26:29],
                 diag=diag, eps=0.05, G=1.0, dt=1e-3)
 
 
@@ -285,5 +333,7 @@ def test_golden_fixture_reproduced(oracle):
     assert np.array_equal(p, g["kdk_pos"]) and np.array_equal(v, g["kdk_vel"])
     p, v, _ = oracle.rk4(g["pos"], g["vel"], g["mass"], g["eps"], g["G"], g["dt"], 3)
     assert np.array_equal(p, g["rk4_pos"]) and np.array_equal(v, g["rk4_vel"])
+    p, v, _, _ = oracle.fr4(g["pos"], g["vel"], g["mass"], g["eps"], g["G"], g["dt"], 3)
+    assert np.array_equal(p, g["fr4_pos"]) and np.array_equal(v, g["fr4_vel"])
     d = oracle.diag(g["pos"], g["vel"], g["mass"], g["eps"], g["G"])
     assert np.array_equal(np.array([d["E"], d["K"], d["W"], *d["P"], *d["L"]]), g["diag"])
