@@ -36,14 +36,21 @@ EPS, DT = 0.02, 5e-4
 SMS, FP64_PER_CLK, FP32_PER_CLK, SM_MAX_GHZ = 152, 2, 128, 2.07
 # derived ALU peaks (flop/s): SMs x lanes-per-clock x 2 (FMA) x max SM clock
 FP64_PEAK_TFLOPS = SMS * FP64_PER_CLK * 2 * SM_MAX_GHZ / 1e3
+# FP64-pipe instruction rate (instructions/s) and the FP64 instructions the two
+# binary64 force paths issue per interaction: 10 one-sided (3 DADD, 3 DFMA for
+# |d|^2 + eps^2, 3 DFMA + 1 DADD for the sums); 14 per pair evaluated once for
+# both particles, i.e. 7 per interaction
+FP64_PIPE_GINSTR = SMS * FP64_PER_CLK * SM_MAX_GHZ
+FP64_INSTR_PER_INTERACTION = {False: 10, True: 7}
 FP32_PEAK_TFLOPS = SMS * FP32_PER_CLK * 2 * SM_MAX_GHZ / 1e3
 
 
 # DRAM traffic of one FP64 force launch at N = 2^20 (dram__bytes_read.sum +
 # dram__bytes_write.sum from one full-size ncu capture; see the k_force_f64 DRAM
 # profile summary).  It is reported only while the kernel's source is the one
-# that was captured: `src_sha` hashes rsqrt_f64, body_f64 and k_force_f64.
-TRAFFIC = {"k_force_f64": {"bytes": 48.11e6 + 61.81e6, "n": 2 ** 20, "src_sha": "7928581e6e417cdd"}}
+# that was captured: `src_sha` hashes rsqrt_recip_sig, mul_sig, body_f64 and
+# k_force_f64.
+TRAFFIC = {"k_force_f64": {"bytes": 47.05e6 + 62.96e6, "n": 2 ** 20, "src_sha": "01dc06074becbf43"}}
 
 
 def _kernel_src_sha(names):
@@ -63,7 +70,9 @@ def _kernel_src_sha(names):
     return hashlib.sha256("\n".join(parts).encode()).hexdigest()[:16]
 
 
-def traffic_f64(n):
+def traffic_f64(n, sym=False):
+    if sym:
+        return None
     t = TRAFFIC["k_force_f64"]
     sha = _kernel_src_sha(["__device__ __forceinline__ void rsqrt_recip_sig(",
                            "__device__ __forceinline__ uint64_t mul_sig(",
@@ -354,6 +363,7 @@ def run_gpu(args):
                 "dLz_over_Lz0": max(abs(d["L"][2] / L0 - 1) for d in ds)}
 
     fms = fp64["force_ms"]
+    sym = fp64["sim"].get_symmetric()[1]
     achieved_tf = inter * FLOP_PER_INTERACTION / (fms * 1e-3) / 1e12
     per = sorted(fp64["per_step"])
     line = {
@@ -363,17 +373,28 @@ def run_gpu(args):
         "config": {"workload": workload_desc(n), "n": n, "mode": "fp64", "scheme": "kdk",
                    "l2": "flushed between timed steps (256 MB device write)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "launch": fp64["sim"].get_launch()},
+                   "launch": {**fp64["sim"].get_launch(), "each_pair_once": sym}},
         "p50_step_ms": float(np.percentile(per, 50)), "p99_step_ms": float(np.percentile(per, 99)),
-        "roofline": {"bound": "alu", "kernel": "k_force_f64", "achieved": achieved_tf,
+        "roofline": {"bound": "alu", "kernel": "k_force_f64_sym" if sym else "k_force_f64",
+                     "achieved": achieved_tf,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": traffic_f64(n),
-                     "traffic_note": "DRAM bytes per launch from one full-size ncu capture; the O(N) "
-                                     "algorithmic bytes (32 B in + S x 32 B partials out per particle) "
+                     "traffic": traffic_f64(n, sym),
+                     "traffic_note": "DRAM bytes per force evaluation from one full-size ncu capture; the "
+                                     "O(N) algorithmic bytes (32 B in + partial sums out per particle) "
                                      "mostly stay in the 129 MB L2",
-                     "flop_convention": f"{FLOP_PER_INTERACTION} flop/interaction x N^2 per launch",
+                     "flop_convention": f"{FLOP_PER_INTERACTION} flop/interaction x N^2 per force evaluation"
+                                        + ("; each pair is evaluated once for both particles, so the "
+                                           "convention can exceed the FP64 peak: fp64_pipe.frac is the "
+                                           "utilisation of the bounding pipe" if sym else ""),
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                     "force_ms_per_launch": fms, "force_share_of_step": fms / ms64},
+                     "fp64_pipe": {"instr_per_interaction": FP64_INSTR_PER_INTERACTION[sym],
+                                   "achieved_ginstr_s": inter * FP64_INSTR_PER_INTERACTION[sym]
+                                   / (fms * 1e-3) / 1e9,
+                                   "peak_ginstr_s": FP64_PIPE_GINSTR,
+                                   "frac": inter * FP64_INSTR_PER_INTERACTION[sym] / (fms * 1e-3) / 1e9
+                                   / FP64_PIPE_GINSTR},
+                     "force_ms_per_launch": fms, "force_ms_note": "one force evaluation (all its launches)",
+                     "force_share_of_step": fms / ms64},
         "gpu_launches": fp64["launches"] * world,
         "clocks": fp64["clocks"],
         "e2e": {"value": world * inter / e2e64["sec"] / 1e9, "unit": UNIT,
@@ -451,7 +472,7 @@ def run_drift(args):
     dt = args.drift_dt
     out = {"drift": args.drift, "scheme": args.drift_scheme, "n": args.n, "eps": EPS, "dt": dt,
            "steps": args.drift_steps, "every": args.drift_every, "workload": workload_desc(args.n),
-           "force_evaluations": args.drift_steps * (4 if args.drift_scheme == "rk4" else 1)}
+           "force_evaluations": args.drift_steps * {"kdk": 1, "fr4": 3, "rk4": 4}[args.drift_scheme]}
     with nb.Simulation(args.n, mode=args.drift, eps=EPS) as sim:
         sim.set_state(w["pos"], w["vel"], w["mass"])
         d0 = sim.diagnostics()
@@ -490,7 +511,7 @@ def main():
     ap.add_argument("--drift", choices=["fp64", "f64e", "mixed", "fp32"], default=None,
                     help="long conservation run of the workload in this mode (Table 2 quantities)")
     ap.add_argument("--drift-steps", type=int, default=10000)
-    ap.add_argument("--drift-scheme", choices=["kdk", "rk4"], default="kdk")
+    ap.add_argument("--drift-scheme", choices=["kdk", "fr4", "rk4"], default="kdk")
     ap.add_argument("--drift-dt", type=float, default=DT)
     ap.add_argument("--drift-every", type=int, default=100)
     ap.add_argument("--profile-force", choices=["fp64", "f64e", "mixed", "fp32"], default=None,

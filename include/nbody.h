@@ -59,6 +59,11 @@ extern "C" {
 #define NBODY_KDK 0    /* Eq. 5-7 (section 1): predictor, drift, one force evaluation, corrector */
 #define NBODY_RK4 1    /* the paper's fourth-order scheme (abstract), read as classical
                           Runge-Kutta on (r, v): four force evaluations per step */
+#define NBODY_FR4 2    /* the other reading of that scheme: the fourth-order symplectic
+                          composition of the KDK step (Yoshida 1990; Forest and Ruth 1990),
+                          three KDK steps of w1 dt, w0 dt, w1 dt with w1 = 1/(2 - 2^(1/3)),
+                          w0 = 1 - 2 w1 (binary64 roundings of the exact values): three
+                          force evaluations per step */
 
 typedef struct nbody_ctx nbody_ctx;
 
@@ -142,9 +147,10 @@ int nbody_get_accel(nbody_ctx *ctx, double *acc, double *pot, int on_device);
 
 /*
  * Advance the state nsteps steps of size dt with `scheme` (NBODY_KDK: Eq. 5-7;
- * NBODY_RK4: classical Runge-Kutta).  KDK needs a(t) before its first step
- * (Eq. 5): it is evaluated once when stale, so nsteps KDK steps cost
- * nsteps + 1 force evaluations the first time and nsteps afterwards.
+ * NBODY_RK4: classical Runge-Kutta; NBODY_FR4: the fourth-order composition of
+ * Eq. 5-7).  KDK and FR4 need a(t) before their first step (Eq. 5): it is
+ * evaluated once when stale, so nsteps KDK steps cost nsteps + 1 force
+ * evaluations the first time and nsteps afterwards (FR4: 3 nsteps + 1, 3 nsteps).
  * Stream-ordered: returns once the work is queued.
  * Errors: EINVAL (unknown scheme, dt <= 0 or non-finite, nsteps < 0),
  * ESTATE, ECUDA.
@@ -179,6 +185,20 @@ int nbody_set_launch(nbody_ctx *ctx, int ipt, int jsplit);
 
 /* Current launch shape actually used for this context's n (outputs may be NULL). */
 int nbody_get_launch(nbody_ctx *ctx, int *ipt, int *jsplit, int *threads, int *tile);
+
+/*
+ * FP64 mode only: evaluate each unordered pair once and apply it to both
+ * particles (Newton's third law; the same binary64 terms with opposite signs,
+ * summed in a different fixed order than the one-sided kernel, so results
+ * differ from it by rounding only and stay deterministic).  mode = -1 (default):
+ * automatic, used when n spans at least 64 blocks of 512 particles; 0: never;
+ * 1: whenever n spans at least 2 blocks.  The launch shape of nbody_set_launch
+ * does not apply to this path.
+ * Errors: EINVAL (NULL context, mode outside -1..1, mode 1 outside FP64).
+ */
+int nbody_set_symmetric(nbody_ctx *ctx, int mode);
+/* The setting (-1, 0, 1) and whether the next force evaluation uses the path. */
+int nbody_get_symmetric(const nbody_ctx *ctx, int *mode, int *active);
 
 /* Number of kernel launches this context has issued since creation. */
 int64_t nbody_launch_count(const nbody_ctx *ctx);

@@ -1,7 +1,8 @@
 """GB300 direct-summation N-body library: Python binding of libnbody.so.
 
 The computation (Eq. 1-2 force and potential, Eq. 5-7 KDK leapfrog, the
-fourth-order scheme, Eq. 8-10 diagnostics) runs in the CUDA kernels of
+fourth-order scheme as classical RK4 or as the symplectic composition of the
+KDK step, Eq. 8-10 diagnostics) runs in the CUDA kernels of
 csrc/ behind the C ABI declared in include/nbody.h.  This module only
 marshals arguments: it turns numpy arrays or torch tensors into pointers,
 picks the current torch CUDA stream, and turns error codes into exceptions.
@@ -18,11 +19,11 @@ import os
 import numpy as np
 
 from . import _abi
-from ._abi import (F64E, FP32, FP64, KDK, MIXED, RK4, NbodyError, check, lib,  # noqa: F401
+from ._abi import (F64E, FP32, FP64, FR4, KDK, MIXED, RK4, NbodyError, check, lib,  # noqa: F401
                    library_path)
 
 MODES = {"fp64": FP64, "mixed": MIXED, "fp32": FP32, "f64e": F64E}
-SCHEMES = {"kdk": KDK, "rk4": RK4}
+SCHEMES = {"kdk": KDK, "rk4": RK4, "fr4": FR4}
 
 __all__ = ["Simulation", "NbodyError", "MODES", "SCHEMES", "lib", "library_path", "build"]
 
@@ -178,6 +179,16 @@ class Simulation:
 
     def set_launch(self, ipt=0, jsplit=0):
         check(lib.nbody_set_launch(self._h, int(ipt), int(jsplit)), "nbody_set_launch")
+
+    def set_symmetric(self, mode=-1):
+        """FP64: evaluate each pair once for both particles (-1 auto, 0 off, 1 on)."""
+        check(lib.nbody_set_symmetric(self._h, int(mode)), "nbody_set_symmetric")
+
+    def get_symmetric(self):
+        """(setting, whether the next force evaluation uses the each-pair-once path)."""
+        m, a = ctypes.c_int(), ctypes.c_int()
+        check(lib.nbody_get_symmetric(self._h, ctypes.byref(m), ctypes.byref(a)), "nbody_get_symmetric")
+        return m.value, bool(a.value)
 
     def get_launch(self):
         v = [ctypes.c_int() for _ in range(4)]

@@ -18,7 +18,7 @@ lib = ctypes.CDLL(library_path)
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, ENOSPC = 0, -1, -2, -3, -4, -5, -6
 FP64, MIXED, FP32, F64E = 0, 1, 2, 3
-KDK, RK4 = 0, 1
+KDK, RK4, FR4 = 0, 1, 2
 
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -44,6 +44,8 @@ _SIGS = {
     "nbody_set_launch": (_i, [_vp, _i, _i]),
     "nbody_get_launch": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                               ctypes.POINTER(_i)]),
+    "nbody_set_symmetric": (_i, [_vp, _i]),
+    "nbody_get_symmetric": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "nbody_launch_count": (_i64, [_vp]),
     "nbody_profile": (_i, [_vp, _i]),
     "nbody_profile_read": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_i64)]),

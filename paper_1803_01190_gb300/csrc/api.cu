@@ -4,6 +4,7 @@
 // stream; nothing here computes on the host.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -45,6 +46,13 @@ struct nbody_ctx {
   double timeout_s = 0;
   int64_t launches = 0;
   bool prof = false;
+  // FP64 each-pair-once path: -1 auto, 0 off, 1 on; diagonal-block units,
+  // per-diagonal row/column buffers (2 x sym_d x n entries)
+  int sym = -1;
+  nb::Unit *sym_units = nullptr;
+  int sym_units_m = 0;
+  void *sym_buf = nullptr;
+  int sym_d = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;  // all created events
   size_t ev_used = 0;                                          // pairs recorded since last read
 };
@@ -134,9 +142,96 @@ static int ensure_part(nbody_ctx *c, int S) {
   return NBODY_OK;
 }
 
+// Blocks (of sym_block_particles()) below which the automatic choice keeps
+// the one-sided kernel: with few blocks the diagonals hold too few work items
+// to fill the GPU (measured on GB300: 43.6 against 55.9 Gint/s at 32 blocks,
+// N = 2^14; 68.5 against 56.6 at 64 blocks, N = 2^15).
+static const int SYM_AUTO_MIN_BLOCKS = 64;
+
+static int sym_blocks(const nbody_ctx *c) {
+  const int B = nb::sym_block_particles();
+  return (int)((c->n + B - 1) / B);
+}
+
+static bool use_sym(const nbody_ctx *c) {
+  if (c->mode != NBODY_FP64 || c->sym == 0) return false;
+  return c->sym == 1 ? sym_blocks(c) >= 2 : sym_blocks(c) >= SYM_AUTO_MIN_BLOCKS;
+}
+
+// FP64, each pair once: slice 0 of c->part = pairs inside each block (the
+// one-sided kernel on the M diagonal blocks), slice 1 = row sums and slice 2 =
+// column sums of the M (M - 1) / 2 pairs of distinct blocks, added over the
+// block diagonals in order.
+static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
+  const int B = nb::sym_block_particles();
+  const int M = sym_blocks(c);
+  const int nd = M / 2;
+  int rc = ensure_part(c, 3);
+  if (rc) return rc;
+  if (c->sym_units_m != M) {
+    if (c->sym_units) cudaFree(c->sym_units);
+    c->sym_units = nullptr;
+    c->sym_units_m = 0;
+    std::vector<nb::Unit> u((size_t)M);
+    for (int I = 0; I < M; I++) {
+      u[I].i0 = u[I].j0 = u[I].out = (int64_t)I * B;
+      u[I].ni = u[I].nj = (int32_t)std::min<int64_t>(B, c->n - (int64_t)I * B);
+      u[I].anchor = 0;
+      u[I].eps2 = c->eps * c->eps;
+    }
+    if (cudaMalloc(&c->sym_units, sizeof(nb::Unit) * M) != cudaSuccess)
+      return fail(NBODY_ENOMEM, "diagonal-block units");
+    CK(cudaMemcpy(c->sym_units, u.data(), sizeof(nb::Unit) * M, cudaMemcpyHostToDevice));
+    c->sym_units_m = M;
+  }
+  if (!c->sym_d && nd > 0) {
+    // enough work items per launch for ~32 waves, within 1 GiB of buffers
+    const int64_t slots = (int64_t)c->num_sms * std::max(1, nb::sym_blocks_per_sm());
+    int64_t D = (32 * slots + M - 1) / M;
+    const int64_t cap = std::max<int64_t>(1, ((int64_t)1 << 30) / (64 * c->n));
+    D = std::max<int64_t>(1, std::min<int64_t>({D, cap, (int64_t)nd}));
+    if (cudaMalloc(&c->sym_buf, (size_t)2 * D * c->n * sizeof(nb::d4)) != cudaSuccess)
+      return fail(NBODY_ENOMEM, "row/column buffers");
+    c->sym_d = (int)D;
+  }
+  CK(nb::launch_force_units(NBODY_FP64, posm_in, nullptr, nullptr, c->sym_units, M, nb::sym_r(),
+                            c->part, 0, c->st));
+  c->launches++;
+  S = 1;
+  if (nd == 0) return NBODY_OK;
+  nb::d4 *part = (nb::d4 *)c->part;
+  nb::d4 *rows = (nb::d4 *)c->sym_buf, *cols = rows + (int64_t)c->sym_d * c->n;
+  for (int d0 = 1; d0 <= nd; d0 += c->sym_d) {
+    const int D = std::min(c->sym_d, nd - d0 + 1);
+    CK(nb::launch_force_f64_sym((const nb::d4 *)posm_in, c->n, c->eps * c->eps, M, d0, D, rows,
+                                cols, c->st));
+    CK(nb::launch_sym_combine(rows, cols, D, c->n, part + c->n, part + 2 * c->n, d0 == 1, c->st));
+    c->launches += 2;
+  }
+  S = 3;
+  return NBODY_OK;
+}
+
 // Raw force sums of the positions in posm_in into c->part; returns the number
-// of segments written through S.
+// of partial slices written through S.
 static int force(nbody_ctx *c, const void *posm_in, int &S) {
+  std::pair<cudaEvent_t, cudaEvent_t> *ev = nullptr;
+  if (c->prof) {
+    if (c->ev_used == c->ev_pool.size()) {
+      std::pair<cudaEvent_t, cudaEvent_t> p;
+      CK(cudaEventCreate(&p.first));
+      CK(cudaEventCreate(&p.second));
+      c->ev_pool.push_back(p);
+    }
+    ev = &c->ev_pool[c->ev_used++];
+  }
+  if (use_sym(c)) {
+    if (ev) CK(cudaEventRecord(ev->first, c->st));
+    int rc = force_sym(c, posm_in, S);
+    if (rc) return rc;
+    if (ev) CK(cudaEventRecord(ev->second, c->st));
+    return NBODY_OK;
+  }
   const int64_t seg = seg_len(c, S);
   int rc = ensure_part(c, S);
   if (rc) return rc;
@@ -155,17 +250,7 @@ static int force(nbody_ctx *c, const void *posm_in, int &S) {
   in.part = c->part;
   nb::Shape sh = c->shape;
   sh.s = S;
-  std::pair<cudaEvent_t, cudaEvent_t> *ev = nullptr;
-  if (c->prof) {
-    if (c->ev_used == c->ev_pool.size()) {
-      std::pair<cudaEvent_t, cudaEvent_t> p;
-      CK(cudaEventCreate(&p.first));
-      CK(cudaEventCreate(&p.second));
-      c->ev_pool.push_back(p);
-    }
-    ev = &c->ev_pool[c->ev_used++];
-    CK(cudaEventRecord(ev->first, c->st));
-  }
+  if (ev) CK(cudaEventRecord(ev->first, c->st));
   CK(nb::launch_force(c->mode, in, sh, c->st));
   c->launches++;
   if (ev) CK(cudaEventRecord(ev->second, c->st));
@@ -207,7 +292,7 @@ static void free_all(nbody_ctx *c) {
   c->ev_pool.clear();
   void *ptrs[] = {c->posm[0], c->posm[1], c->vel, c->vbar, c->acc, c->part, c->rk_vs, c->rk_sr,
                   c->rk_sv, c->tmp_posm, c->tmp_acc, c->fpos, c->anchor, c->diag_blocks,
-                  c->diag_out, c->d_flag, c->stage};
+                  c->diag_out, c->d_flag, c->stage, c->sym_units, c->sym_buf};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_diag) cudaFreeHost(c->h_diag);
@@ -429,30 +514,48 @@ int nbody_get_accel(nbody_ctx *c, double *acc, double *pot, int on_device) {
   return copy_acc_out(c, c->acc, acc, pot, on_device);
 }
 
-static int step_kdk(nbody_ctx *c, double dt, int64_t nsteps) {
+// nsteps steps of size dt, each a sequence of nh KDK steps (Eq. 5-7) of sizes
+// h[0..nh-1] (KDK: one of dt; FR4: w1 dt, w0 dt, w1 dt).  Each force
+// evaluation is followed by one fused kernel: the corrector of the KDK step
+// that ended and the predictor of the next one.
+static int step_kdk_seq(nbody_ctx *c, const double *h, int nh, double dt, int64_t nsteps) {
   int rc = ensure_acc(c);
   if (rc) return rc;
   const int nxt = 1 - c->cur;
-  if (!(c->pred_valid && c->pred_dt == dt)) {
-    CK(nb::launch_kdk_predict(c->mode, c->n, dt, c->posm[c->cur], c->vel, c->acc, c->vbar,
+  if (!(c->pred_valid && c->pred_dt == h[0])) {
+    CK(nb::launch_kdk_predict(c->mode, c->n, h[0], c->posm[c->cur], c->vel, c->acc, c->vbar,
                               c->posm[nxt], c->st));
     c->launches++;
     c->pred_valid = true;
-    c->pred_dt = dt;
+    c->pred_dt = h[0];
   }
   for (int64_t k = 0; k < nsteps; k++) {
-    const int a = c->cur, b = 1 - c->cur;  // posm[b] holds r(t+dt)
-    int S = 0;
-    rc = force(c, c->posm[b], S);
-    if (rc) return rc;
-    CK(nb::launch_kdk_correct_predict(c->mode, epi(c, S), dt, c->acc, c->posm[b], c->vel, c->vbar,
-                                      c->posm[a], c->st));
-    c->launches++;
-    c->cur = b;
+    for (int s = 0; s < nh; s++) {
+      const int a = c->cur, b = 1 - c->cur;  // posm[b] holds the predicted positions
+      int S = 0;
+      rc = force(c, c->posm[b], S);
+      if (rc) return rc;
+      CK(nb::launch_kdk_correct_predict(c->mode, epi(c, S), h[s], h[(s + 1) % nh], c->acc,
+                                        c->posm[b], c->vel, c->vbar, c->posm[a], c->st));
+      c->launches++;
+      c->cur = b;
+    }
     c->t += dt;
     c->step++;
   }
   return NBODY_OK;
+}
+
+static int step_kdk(nbody_ctx *c, double dt, int64_t nsteps) {
+  return step_kdk_seq(c, &dt, 1, dt, nsteps);
+}
+
+// Fourth-order composition (Yoshida 1990; Forest and Ruth 1990): the weights
+// are the binary64 roundings of 1/(2 - 2^(1/3)) and -2^(1/3)/(2 - 2^(1/3)).
+static int step_fr4(nbody_ctx *c, double dt, int64_t nsteps) {
+  const double w1 = 0x1.59e8b6eb96338p+0, w0 = -0x1.b3d16dd72c671p+0;
+  const double h[3] = {w1 * dt, w0 * dt, w1 * dt};
+  return step_kdk_seq(c, h, 3, dt, nsteps);
 }
 
 static int step_rk4(nbody_ctx *c, double dt, int64_t nsteps) {
@@ -484,13 +587,17 @@ static int step_rk4(nbody_ctx *c, double dt, int64_t nsteps) {
 
 int nbody_step(nbody_ctx *c, int scheme, double dt, int64_t nsteps) {
   if (!c) return fail(NBODY_EINVAL, "NULL context");
-  if (scheme != NBODY_KDK && scheme != NBODY_RK4) return fail(NBODY_EINVAL, "unknown scheme");
+  if (scheme != NBODY_KDK && scheme != NBODY_RK4 && scheme != NBODY_FR4)
+    return fail(NBODY_EINVAL, "unknown scheme");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(NBODY_EINVAL, "dt must be finite and > 0");
   if (nsteps < 0) return fail(NBODY_EINVAL, "nsteps < 0");
   if (!c->has_state) return fail(NBODY_ESTATE, "step before set_state");
   CK(cudaSetDevice(c->device));
-  nvtxRangePushA(scheme == NBODY_KDK ? "nbody_step KDK" : "nbody_step RK4");
-  const int rc = scheme == NBODY_KDK ? step_kdk(c, dt, nsteps) : step_rk4(c, dt, nsteps);
+  nvtxRangePushA(scheme == NBODY_KDK ? "nbody_step KDK"
+                 : scheme == NBODY_RK4 ? "nbody_step RK4" : "nbody_step FR4");
+  const int rc = scheme == NBODY_KDK   ? step_kdk(c, dt, nsteps)
+                 : scheme == NBODY_RK4 ? step_rk4(c, dt, nsteps)
+                                       : step_fr4(c, dt, nsteps);
   nvtxRangePop();
   return rc;
 }
@@ -538,6 +645,21 @@ int nbody_get_launch(nbody_ctx *c, int *ipt, int *jsplit, int *threads, int *til
   if (jsplit) *jsplit = S;
   if (threads) *threads = c->shape.bt;
   if (tile) *tile = c->shape.t;
+  return NBODY_OK;
+}
+
+int nbody_set_symmetric(nbody_ctx *c, int mode) {
+  if (!c) return fail(NBODY_EINVAL, "NULL context");
+  if (mode < -1 || mode > 1) return fail(NBODY_EINVAL, "symmetric mode must be -1, 0 or 1");
+  if (mode == 1 && c->mode != NBODY_FP64) return fail(NBODY_EINVAL, "each-pair-once path is FP64 only");
+  c->sym = mode;
+  return NBODY_OK;
+}
+
+int nbody_get_symmetric(const nbody_ctx *c, int *mode, int *active) {
+  if (!c) return fail(NBODY_EINVAL, "NULL context");
+  if (mode) *mode = c->sym;
+  if (active) *active = use_sym(c) ? 1 : 0;
   return NBODY_OK;
 }
 

@@ -40,6 +40,7 @@
 //         thread's packed accumulators (even and odd j) are added at the end.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "nbody_internal.cuh"
@@ -286,6 +287,203 @@ __global__ void __launch_bounds__(BT) k_force_f64(const d4 *__restrict__ posm, W
       const int li = r * BT + tid;
       if (li < u.ni) part[u.out + li] = d4{ax[r], ay[r], az[r], pt[r]};
     }
+  }
+}
+
+// ---------------------------------------------------------------- binary64, each pair once
+// Newton's third law: the pair (i, j) contributes m_j d / w to a_i and
+// -m_i d / w to a_j with the same d = r_j - r_i and w = (|d|^2 + eps^2)^{3/2},
+// so one evaluation of d, |d|^2 + eps^2, 1/r and 1/r^2 serves both: 14 FP64
+// instructions for two interactions instead of 20.
+//
+// Particles are cut into M blocks of B = BT*R.  A work item (d, I), d >= 1,
+// pairs i-block I with j-block J = (I + d) mod M; d = 1 .. floor(M/2) covers
+// every unordered pair of distinct blocks once (for d = M/2 with M even, only
+// I < M/2 computes; the other items write zeros).  For a fixed d every block
+// is the row block of one item and the column block of one item, so the
+// item's row sums (block I) and column sums (block J) each own a slice of the
+// per-diagonal buffers rows[dl], cols[dl] without any atomic or race; the
+// slices are added in diagonal order afterwards (deterministic).  Pairs
+// inside a block (d = 0) run through the one-sided kernel.
+//
+// Column sums: i stays in registers (R per thread); a j-tile of T particles
+// is in shared memory and is walked in chunks of 32.  At step k of a chunk,
+// lane l works on j = (l + k) mod 32 with its R i-particles and then hands the
+// running sum of that j to lane l - 1, so after 32 steps lane l holds the sum
+// over the warp's i-particles of j = l.  The warps' sums are then added in a
+// fixed order in shared memory.
+__device__ __noinline__ double2 rq_f64_slow(double r2) {
+  return make_double2(1.0 / sqrt(r2), 1.0 / r2);
+}
+
+struct MassSig {
+  uint64_t A;  // 53-bit significand
+  int e;       // biased exponent
+  bool fast;   // in [2^-895, 2^897): the integer multiply applies
+};
+__device__ __forceinline__ MassSig mass_sig(double m) {
+  const unsigned mh = (unsigned)__double2hiint(m);
+  MassSig s;
+  s.A = ((uint64_t)((mh & 0xFFFFFu) | 0x100000u) << 32) | (unsigned)__double2loint(m);
+  s.e = (int)(mh >> 20);
+  s.fast = (mh >> 20) - 128u < 1793u;
+  return s;
+}
+
+// m/r and (m/r)/r^2 from the integer 1/r, 1/r^2 (or, for masses outside the
+// integer range, binary64 products of their packed values)
+__device__ __forceinline__ void scale_pair(double m, const MassSig &ms, uint64_t R, int ER,
+                                           uint64_t Q, int EQ, double &my, double &f) {
+  if (ms.fast) {
+    int emy, ef;
+    const uint64_t smy = mul_sig(ms.A, ms.e, R, ER, emy);
+    const uint64_t sf = mul_sig(smy, emy, Q, EQ, ef);
+    my = pack_f64(smy, emy);
+    f = pack_f64(sf, ef);
+  } else {
+    my = m * pack_f64(R, ER);
+    f = my * pack_f64(Q, EQ);
+  }
+}
+
+__device__ __forceinline__ void body_f64_sym(const d4 &pj, const MassSig &mj, double xi,
+                                             double yi, double zi, double mi,
+                                             const MassSig &msi, double eps2, double &ax,
+                                             double &ay, double &az, double &pt, double &gx,
+                                             double &gy, double &gz, double &gp) {
+  const double dx = pj.x - xi, dy = pj.y - yi, dz = pj.z - zi;
+  const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+  const unsigned hi = (unsigned)__double2hiint(r2);
+  double my, f, myj, fj;
+  if (hi - 0x3C300000u < 0x43B00000u - 0x3C300000u) {
+    uint64_t R, Q;
+    int ER, EQ;
+    rsqrt_recip_sig(hi, (unsigned)__double2loint(r2), R, ER, Q, EQ);
+    scale_pair(pj.w, mj, R, ER, Q, EQ, my, f);
+    scale_pair(mi, msi, R, ER, Q, EQ, myj, fj);
+  } else {
+    const double2 v = rq_f64_slow(r2);
+    my = pj.w * v.x;
+    f = my * v.y;
+    myj = mi * v.x;
+    fj = myj * v.y;
+  }
+  ax = fma(dx, f, ax);
+  ay = fma(dy, f, ay);
+  az = fma(dz, f, az);
+  pt += my;
+  gx = fma(-dx, fj, gx);
+  gy = fma(-dy, fj, gy);
+  gz = fma(-dz, fj, gz);
+  gp += myj;
+}
+
+// Padding beyond n: massless and far away (finite r^2, zero contribution).
+__device__ __forceinline__ d4 pad_or_load(const d4 *posm, int64_t k, int64_t n) {
+  return k < n ? posm[k] : d4{1e30, 1e30, 1e30, 0.0};
+}
+
+template <int BT, int R, int T>
+__global__ void __launch_bounds__(BT) k_force_f64_sym(const d4 *__restrict__ posm, int64_t n,
+                                                      double eps2, int M, int d0,
+                                                      d4 *__restrict__ rows,
+                                                      d4 *__restrict__ cols) {
+  constexpr int B = BT * R, NW = BT / 32;
+  static_assert(T == BT && B % T == 0, "one column sum per thread per tile");
+  __shared__ d4 tile[T];
+  __shared__ d4 colw[NW][T];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int dl = blockIdx.x / M, I = blockIdx.x % M, d = d0 + dl;
+  const int J = (I + d) % M;
+  const int64_t i0 = (int64_t)I * B, j0 = (int64_t)J * B;
+  d4 *rowo = rows + (int64_t)dl * n;
+  d4 *colo = cols + (int64_t)dl * n;
+  if (2 * d == M && I >= M / 2) {  // the pair of blocks is the item (I - M/2, I)
+    for (int k = tid; k < B; k += BT) {
+      if (i0 + k < n) rowo[i0 + k] = d4{0.0, 0.0, 0.0, 0.0};
+      if (j0 + k < n) colo[j0 + k] = d4{0.0, 0.0, 0.0, 0.0};
+    }
+    return;
+  }
+  double xi[R], yi[R], zi[R], mi[R], ax[R], ay[R], az[R], pt[R];
+  MassSig msi[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const d4 p = pad_or_load(posm, i0 + r * BT + tid, n);
+    xi[r] = p.x;
+    yi[r] = p.y;
+    zi[r] = p.z;
+    mi[r] = p.w;
+    msi[r] = mass_sig(p.w);
+    ax[r] = ay[r] = az[r] = pt[r] = 0.0;
+  }
+  for (int t0 = 0; t0 < B; t0 += T) {
+    const int64_t jt = j0 + t0;
+    __syncthreads();
+    for (int k = tid; k < T; k += BT) tile[k] = pad_or_load(posm, jt + k, n);
+    __syncthreads();
+#pragma unroll 1
+    for (int c = 0; c < T; c += 32) {
+      double gx = 0.0, gy = 0.0, gz = 0.0, gp = 0.0;
+#pragma unroll 2
+      for (int k = 0; k < 32; k++) {
+        const d4 pj = tile[c + ((lane + k) & 31)];
+        const MassSig mj = mass_sig(pj.w);
+#pragma unroll
+        for (int r = 0; r < R; r++)
+          body_f64_sym(pj, mj, xi[r], yi[r], zi[r], mi[r], msi[r], eps2, ax[r], ay[r], az[r],
+                       pt[r], gx, gy, gz, gp);
+        const int src = (lane + 1) & 31;
+        gx = __shfl_sync(0xFFFFFFFFu, gx, src);
+        gy = __shfl_sync(0xFFFFFFFFu, gy, src);
+        gz = __shfl_sync(0xFFFFFFFFu, gz, src);
+        gp = __shfl_sync(0xFFFFFFFFu, gp, src);
+      }
+      colw[warp][c + lane] = d4{gx, gy, gz, gp};
+    }
+    __syncthreads();
+    {
+      d4 s = colw[0][tid];
+#pragma unroll
+      for (int w = 1; w < NW; w++) {
+        const d4 v = colw[w][tid];
+        s.x += v.x;
+        s.y += v.y;
+        s.z += v.z;
+        s.w += v.w;
+      }
+      if (jt + tid < n) colo[jt + tid] = s;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const int64_t i = i0 + r * BT + tid;
+    if (i < n) rowo[i] = d4{ax[r], ay[r], az[r], pt[r]};
+  }
+}
+
+// acc_rows[i] (+)= rows[0][i] + ... + rows[D-1][i], the same for the columns,
+// in diagonal order.
+__global__ void k_sym_combine(const d4 *__restrict__ rows, const d4 *__restrict__ cols, int D,
+                              int64_t n, d4 *__restrict__ acc_rows, d4 *__restrict__ acc_cols,
+                              int first) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    d4 a = first ? d4{0.0, 0.0, 0.0, 0.0} : acc_rows[i];
+    d4 b = first ? d4{0.0, 0.0, 0.0, 0.0} : acc_cols[i];
+    for (int k = 0; k < D; k++) {
+      const d4 u = rows[(int64_t)k * n + i], v = cols[(int64_t)k * n + i];
+      a.x += u.x;
+      a.y += u.y;
+      a.z += u.z;
+      a.w += u.w;
+      b.x += v.x;
+      b.y += v.y;
+      b.z += v.z;
+      b.w += v.w;
+    }
+    acc_rows[i] = a;
+    acc_cols[i] = b;
   }
 }
 
@@ -899,6 +1097,34 @@ static cudaError_t launch_w(int mode, int r, const void *posm, const float4 *fpo
     case 8: launch_rw<8>(mode, posm, fpos, anchor, w, grid, part, st); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- binary64, each pair once: launches
+constexpr int SYM_BT = 128, SYM_R = 4, SYM_T = 128;
+
+int sym_block_particles() { return SYM_BT * SYM_R; }
+int sym_r() { return SYM_R; }
+
+int sym_blocks_per_sm() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_f64_sym<SYM_BT, SYM_R, SYM_T>,
+                                                    SYM_BT, 0) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+cudaError_t launch_force_f64_sym(const d4 *posm, int64_t n, double eps2, int M, int d0, int D,
+                                 d4 *rows, d4 *cols, cudaStream_t st) {
+  k_force_f64_sym<SYM_BT, SYM_R, SYM_T><<<D * M, SYM_BT, 0, st>>>(posm, n, eps2, M, d0, rows, cols);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sym_combine(const d4 *rows, const d4 *cols, int D, int64_t n, d4 *acc_rows,
+                               d4 *acc_cols, bool first, cudaStream_t st) {
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  k_sym_combine<<<(unsigned)blocks, 256, 0, st>>>(rows, cols, D, n, acc_rows, acc_cols,
+                                                  first ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -92,6 +92,19 @@ int force_tile(int mode);
 cudaError_t launch_mixed_prep(const d4 *posm, int64_t n, int tile, float4 *fpos, float4 *anchor,
                               cudaStream_t st, bool ff = false);
 int force_max_blocks_per_sm(int mode, const Shape &sh);
+// FP64, each pair once (Newton's third law): blocks of sym_block_particles()
+// particles; launch D diagonals d0 .. d0+D-1 of the M x M block pairs, row
+// sums of diagonal d0+k into rows[k*n ..], column sums into cols[k*n ..];
+// launch_sym_combine adds them (in diagonal order) into acc_rows / acc_cols
+// (overwriting them when first).
+int sym_block_particles();
+int sym_r();
+int sym_blocks_per_sm();
+cudaError_t launch_force_f64_sym(const d4 *posm, int64_t n, double eps2, int M, int d0, int D,
+                                 d4 *rows, d4 *cols, cudaStream_t st);
+cudaError_t launch_sym_combine(const d4 *rows, const d4 *cols, int D, int64_t n, d4 *acc_rows,
+                               d4 *acc_cols, bool first, cudaStream_t st);
+
 bool shape_supported(int mode, const Shape &sh);
 
 // update / epilogue kernels (update.cu)
@@ -111,9 +124,9 @@ cudaError_t launch_unpack_acc(int mode, const void *acc, int64_t n, double *acc3
 cudaError_t launch_kdk_predict(int mode, int64_t n, double dt, const void *posm_cur,
                                const void *vel, const void *acc, void *vbar, void *posm_nxt,
                                cudaStream_t st);
-cudaError_t launch_kdk_correct_predict(int mode, const EpiIn &e, double dt, void *acc,
-                                       void *posm_new, void *vel, void *vbar, void *posm_pred,
-                                       cudaStream_t st);
+cudaError_t launch_kdk_correct_predict(int mode, const EpiIn &e, double dt, double dt_next,
+                                       void *acc, void *posm_new, void *vel, void *vbar,
+                                       void *posm_pred, cudaStream_t st);
 cudaError_t launch_rk4_stage(int mode, const EpiIn &e, int stage, double dt, const void *posm0,
                              void *vel0, void *rk_vs, void *rk_sr, void *rk_sv, void *posm_stage,
                              cudaStream_t st);

@@ -154,11 +154,12 @@ __global__ void k_kdk_predict(int64_t n, real dt, real hdt, const real4<real> *_
 }
 
 // After the force at r(t+dt): a' = G sum(parts); corrector
-//   v(t+dt) = vbar + dt/2 a'           (Eq. 7)
-// then the predictor and drift of the next step into posm_pred.
+//   v(t+dt) = vbar + dt/2 a'           (Eq. 7, chdt = dt/2 of the step just ended)
+// then the predictor and drift of the next step, of size dt_next (the same dt
+// for KDK; the next substep's for the fourth-order composition), into posm_pred.
 template <typename real, typename P>
 __global__ void k_kdk_correct_predict(const P *__restrict__ part, int S, int64_t n, real G,
-                                      real dt, real hdt, real4<real> *__restrict__ acc,
+                                      real chdt, real dt, real hdt, real4<real> *__restrict__ acc,
                                       const real4<real> *__restrict__ posm_new,
                                       real4<real> *__restrict__ vel, real4<real> *__restrict__ vbar,
                                       real4<real> *__restrict__ posm_pred) {
@@ -168,8 +169,8 @@ __global__ void k_kdk_correct_predict(const P *__restrict__ part, int S, int64_t
     const real4<real> a = gather_acc<real, P>(part, S, n, i, G);
     acc[i] = a;
     const real4<real> vb = vbar[i];
-    const real4<real> v = mk4<real>(O::add(vb.x, O::mul(hdt, a.x)), O::add(vb.y, O::mul(hdt, a.y)),
-                                    O::add(vb.z, O::mul(hdt, a.z)), (real)0);
+    const real4<real> v = mk4<real>(O::add(vb.x, O::mul(chdt, a.x)), O::add(vb.y, O::mul(chdt, a.y)),
+                                    O::add(vb.z, O::mul(chdt, a.z)), (real)0);
     vel[i] = v;
     real4<real> nvb, rn;
     kdk_predict_one<real>(dt, hdt, posm_new[i], v, a, nvb, rn);
@@ -362,17 +363,18 @@ cudaError_t launch_kdk_predict(int mode, int64_t n, double dt, const void *posm_
   return cudaGetLastError();
 }
 
-cudaError_t launch_kdk_correct_predict(int mode, const EpiIn &e, double dt, void *acc,
-                                       void *posm_new, void *vel, void *vbar, void *posm_pred,
-                                       cudaStream_t st) {
+cudaError_t launch_kdk_correct_predict(int mode, const EpiIn &e, double dt, double dt_next,
+                                       void *acc, void *posm_new, void *vel, void *vbar,
+                                       void *posm_pred, cudaStream_t st) {
   if (mode == NBODY_FP32)
     k_kdk_correct_predict<float, float4><<<grid_for(e.n), 256, 0, st>>>(
-        (const float4 *)e.part, e.S, e.n, (float)e.G, (float)dt, (float)(dt / 2), (float4 *)acc,
-        (const float4 *)posm_new, (float4 *)vel, (float4 *)vbar, (float4 *)posm_pred);
+        (const float4 *)e.part, e.S, e.n, (float)e.G, (float)(dt / 2), (float)dt_next,
+        (float)(dt_next / 2), (float4 *)acc, (const float4 *)posm_new, (float4 *)vel,
+        (float4 *)vbar, (float4 *)posm_pred);
   else
     k_kdk_correct_predict<double, d4><<<grid_for(e.n), 256, 0, st>>>(
-        (const d4 *)e.part, e.S, e.n, e.G, dt, dt / 2, (d4 *)acc, (const d4 *)posm_new,
-        (d4 *)vel, (d4 *)vbar, (d4 *)posm_pred);
+        (const d4 *)e.part, e.S, e.n, e.G, dt / 2, dt_next, dt_next / 2, (d4 *)acc,
+        (const d4 *)posm_new, (d4 *)vel, (d4 *)vbar, (d4 *)posm_pred);
   return cudaGetLastError();
 }
 

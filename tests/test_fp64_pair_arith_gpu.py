@@ -41,12 +41,13 @@ def _axis_positions(log2_lo, log2_hi, n, seed):
     return pos
 
 
-def _axis_case(nb, m0, pos):
+def _axis_case(nb, m0, pos, sym=-1):
     """(pot ulps, acc ulps, pot) of the test particles against extended precision."""
     x = pos[1:, 0]
     mass = np.zeros(len(pos))
     mass[0] = m0
     with nb.Simulation(len(mass), "fp64", eps=0.0) as sim:
+        sim.set_symmetric(sym)
         acc, pot = sim.accel(pos, mass)
     r2 = (x * x).astype(np.longdouble)  # the binary64 square, as the kernel forms it
     inv_r = 1 / np.sqrt(r2)
@@ -66,21 +67,24 @@ def test_longdouble_is_extended():
     assert np.finfo(np.longdouble).nmant >= 63
 
 
+@pytest.mark.parametrize("sym", [0, 1])
 @pytest.mark.parametrize("seed", [1, 2])
-def test_unit_mass_potential_is_reciprocal_sqrt(nb, seed):
-    # |r^2| in [2^-59, 2^59]: the integer path; m = 1 makes pot exactly -(1/r)
+def test_unit_mass_potential_is_reciprocal_sqrt(nb, seed, sym):
+    # |r^2| in [2^-59, 2^59]: the integer path; m = 1 makes pot exactly -(1/r);
+    # sym = 1: each pair evaluated once for both particles
     pos = _axis_positions(-29.5, 29.5, 40000, 20180200 + seed)
-    pot_ulp, acc_ulp, _ = _axis_case(nb, 1.0, pos)
+    pot_ulp, acc_ulp, _ = _axis_case(nb, 1.0, pos, sym)
     assert pot_ulp.max() <= 0.55, pot_ulp.max()
     assert 0.2 <= pot_ulp.mean() <= 0.3  # near correctly rounded on average
     assert acc_ulp.max() <= 4.1, acc_ulp.max()
 
 
-def test_general_mass_product_is_binary64(nb):
+@pytest.mark.parametrize("sym", [0, 1])
+def test_general_mass_product_is_binary64(nb, sym):
     pos = _axis_positions(-29.5, 29.5, 40000, 20180203)
-    _, _, pot1 = _axis_case(nb, 1.0, pos)
+    _, _, pot1 = _axis_case(nb, 1.0, pos, sym)
     m0 = 0.7371089013468521
-    pot_ulp, acc_ulp, pot = _axis_case(nb, m0, pos)
+    pot_ulp, acc_ulp, pot = _axis_case(nb, m0, pos, sym)
     # the integer multiply rounds m (1/r) exactly as binary64 does
     assert np.array_equal(pot, m0 * pot1)
     assert pot_ulp.max() <= 1.6, pot_ulp.max()

@@ -108,6 +108,9 @@ def test_golden_fixture(nb):
         sim.set_state(g["pos"], g["vel"], g["mass"])
         sim.step(g["dt"], 3, "rk4")
         rp, rv, _, _ = sim.get_state()
+        sim.set_state(g["pos"], g["vel"], g["mass"])
+        sim.step(g["dt"], 3, "fr4")
+        fp, fv, _, _ = sim.get_state()
     _, _, smag = oracle.accel(g["pos"], g["mass"], g["eps"])
     assert fp64_accel_gate(acc, g["acc"], smag, n)[0].all()
     assert np.allclose(pot, g["pot"], rtol=1e-12, atol=0)
@@ -117,7 +120,64 @@ def test_golden_fixture(nb):
     assert np.abs(kv - g["kdk_vel"]).max() <= 1e-12 * vscale
     assert np.abs(rp - g["rk4_pos"]).max() <= 1e-12 * scale
     assert np.abs(rv - g["rk4_vel"]).max() <= 1e-12 * vscale
+    assert np.abs(fp - g["fr4_pos"]).max() <= 1e-12 * scale
+    assert np.abs(fv - g["fr4_vel"]).max() <= 1e-12 * vscale
     assert abs(d["E"] - g["diag"][0]) <= 1e-13 * abs(g["diag"][0])
+
+
+# ------------------------------------------------------------------ FP64, each pair once
+# 512-particle blocks: n = 513, 1024 (M = 2: the half diagonal d = M/2), 1100 (M = 3),
+# 1537 (M = 4), 2559 (M = 5), 4099 (M = 9, ragged tail of 3)
+@pytest.mark.parametrize("n", [513, 1024, 1100, 1537, 2559, 4099])
+@pytest.mark.parametrize("eps", [0.01, 0.0])
+def test_fp64_symmetric_accel_sizes(nb, n, eps):
+    pos, _, _ = nbody_ics.plummer(n, 31 + n)
+    mass = nbody_ics.lognormal_masses(n, 32 + n)
+    with nb.Simulation(n, "fp64", eps=eps, G=1.3) as sim:
+        sim.set_symmetric(1)
+        assert sim.get_symmetric() == (1, True)
+        acc, pot = sim.accel(pos, mass)
+    _check_fp64(acc, pot, pos, mass, eps, 1.3)
+
+
+def test_fp64_symmetric_auto_and_off(nb):
+    w = nbody_ics.workload("disk_halo", n=40000)
+    with nb.Simulation(40000, "fp64", eps=w["eps"]) as sim:
+        assert sim.get_symmetric() == (-1, True)      # 79 blocks: automatic choice takes it
+        acc_s, pot_s = sim.accel(w["pos"], w["mass"])
+        acc_s2, pot_s2 = sim.accel(w["pos"], w["mass"])
+        sim.set_symmetric(0)
+        assert sim.get_symmetric() == (0, False)
+        acc_o, pot_o = sim.accel(w["pos"], w["mass"])
+    assert np.array_equal(acc_s, acc_s2) and np.array_equal(pot_s, pot_s2)   # deterministic
+    assert not np.array_equal(acc_s, acc_o)                                  # a different order
+    _check_fp64(acc_s, pot_s, w["pos"], w["mass"], w["eps"], rows=np.arange(0, 40000, 97))
+    _check_fp64(acc_o, pot_o, w["pos"], w["mass"], w["eps"], rows=np.arange(0, 40000, 97))
+    with nb.Simulation(20000, "fp64", eps=0.01) as small:
+        assert small.get_symmetric() == (-1, False)   # 40 blocks: one-sided kernel
+    with nb.Simulation(3000, "mixed", eps=0.01) as other:
+        assert other.get_symmetric() == (-1, False)
+        with pytest.raises(nb.NbodyError):
+            other.set_symmetric(1)
+
+
+def test_fp64_symmetric_massless_and_kdk(nb):
+    """Massless tracers (binary64 fallback on their side of each pair) and a
+    KDK trajectory through the each-pair-once path."""
+    n = 2600
+    w = nbody_ics.workload("plummer", n=n)
+    mass = w["mass"].copy()
+    mass[::5] = 0.0
+    with nb.Simulation(n, "fp64", eps=0.01) as sim:
+        sim.set_symmetric(1)
+        acc, pot = sim.accel(w["pos"], mass)
+        _check_fp64(acc, pot, w["pos"], mass, 0.01)
+        sim.set_state(w["pos"], w["vel"], mass)
+        sim.step(1e-3, 3)
+        p, v, _, _ = sim.get_state()
+    op, ov, _, _ = oracle.kdk(w["pos"], w["vel"], mass, 0.01, 1.0, 1e-3, 3)
+    assert np.abs(p - op).max() <= 1e-12 * np.abs(op).max()
+    assert np.abs(v - ov).max() <= 1e-12 * np.abs(ov).max()
 
 
 # ------------------------------------------------------------------ KDK, Eq. 5-7 (Plummer N=4096)
@@ -176,6 +236,79 @@ def test_fp64_rk4(nb):
     assert np.abs(v - ov).max() <= 1e-12 * np.abs(ov).max()
     _, _, smag = oracle.accel(op, w["mass"], 0.01)
     assert fp64_accel_gate(acc, oa, smag, 1000)[0].all()
+
+
+def test_fp64_fr4_each_step(nb):
+    """Fourth-order composition of the KDK step, Plummer N = 2000: state,
+    accelerations and potentials against the oracle after every step."""
+    w = nbody_ics.workload("plummer", n=2000)
+    mass, eps, dt = w["mass"], 0.01, 2e-3
+    op, ov, oa = w["pos"].copy(), w["vel"].copy(), None
+    with nb.Simulation(2000, "fp64", eps=eps) as sim:
+        sim.set_state(w["pos"], w["vel"], mass)
+        for k in range(4):
+            sim.step(dt, 1, "fr4")
+            op, ov, oa, opot = oracle.fr4(op, ov, mass, eps, 1.0, dt, 1, acc0=oa)
+            p, v, t, s = sim.get_state()
+            acc, pot = sim.get_accel()
+            assert s == k + 1 and abs(t - (k + 1) * dt) < 1e-15
+            assert np.abs(p - op).max() <= 1e-12 * np.abs(op).max()
+            assert np.abs(v - ov).max() <= 1e-12 * np.abs(ov).max()
+            _, _, smag = oracle.accel(op, mass, eps)
+            assert fp64_accel_gate(acc, oa, smag, 2000)[0].all()
+            assert np.all(np.abs(pot - opot) <= 1e-12 * np.abs(opot))
+
+
+def test_fr4_multistep_equals_single_steps_and_launches(nb):
+    w = nbody_ics.workload("plummer", n=1200)
+    with nb.Simulation(1200, "fp64", eps=0.01) as a, nb.Simulation(1200, "fp64", eps=0.01) as b:
+        a.set_state(w["pos"], w["vel"], w["mass"])
+        b.set_state(w["pos"], w["vel"], w["mass"])
+        a.step(1e-3, 1, "fr4")
+        l0 = a.launch_count
+        a.step(1e-3, 4, "fr4")
+        per_step = (a.launch_count - l0) / 4
+        for _ in range(5):
+            b.step(1e-3, 1, "fr4")
+        pa, va, _, _ = a.get_state()
+        pb, vb, _, _ = b.get_state()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+    # three force evaluations per step, each followed by one fused update
+    assert per_step == 6, per_step
+
+
+def test_kdk_fr4_rk4_switching(nb):
+    w = nbody_ics.workload("plummer", n=600)
+    args = (w["mass"], 0.02, 1.0)
+    with nb.Simulation(600, "fp64", eps=0.02) as sim:
+        sim.set_state(w["pos"], w["vel"], w["mass"])
+        sim.step(1e-3, 2, "kdk")
+        sim.step(1e-3, 2, "fr4")
+        sim.step(1e-3, 1, "rk4")
+        sim.step(2e-3, 1, "fr4")
+        sim.step(2e-3, 1, "kdk")
+        p, v, t, s = sim.get_state()
+    op, ov, _, _ = oracle.kdk(w["pos"], w["vel"], *args, 1e-3, 2)
+    op, ov, _, _ = oracle.fr4(op, ov, *args, 1e-3, 2)
+    op, ov, _ = oracle.rk4(op, ov, *args, 1e-3, 1)
+    op, ov, _, _ = oracle.fr4(op, ov, *args, 2e-3, 1)
+    op, ov, _, _ = oracle.kdk(op, ov, *args, 2e-3, 1)
+    assert s == 7 and abs(t - 9e-3) < 1e-15
+    assert np.abs(p - op).max() <= 1e-12 * np.abs(op).max()
+    assert np.abs(v - ov).max() <= 1e-12 * np.abs(ov).max()
+
+
+@pytest.mark.parametrize("mode,tol", [("f64e", 1e-12), ("mixed", 1e-6), ("fp32", 1e-4)])
+def test_fr4_reduced_precision_tracks_oracle(nb, mode, tol):
+    w = nbody_ics.workload("plummer", n=3000)
+    with nb.Simulation(3000, mode, eps=0.01) as sim:
+        sim.set_state(w["pos"], w["vel"], w["mass"])
+        sim.step(1e-3, 3, "fr4")
+        p, v, t, s = sim.get_state()
+    op, ov, _, _ = oracle.fr4(w["pos"], w["vel"], w["mass"], 0.01, 1.0, 1e-3, 3)
+    assert s == 3
+    assert np.abs(p - op).max() <= tol * np.abs(op).max()
+    assert np.abs(v - ov).max() <= 100 * tol * np.abs(ov).max()
 
 
 def test_kdk_then_rk4_then_kdk(nb):
