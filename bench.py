@@ -50,7 +50,12 @@ FP32_PEAK_TFLOPS = SMS * FP32_PER_CLK * 2 * SM_MAX_GHZ / 1e3
 # profile summary).  It is reported only while the kernel's source is the one
 # that was captured: `src_sha` hashes rsqrt_recip_sig, mul_sig, body_f64 and
 # k_force_f64.
-TRAFFIC = {"k_force_f64": {"bytes": 47.05e6 + 62.96e6, "n": 2 ** 20, "src_sha": "01dc06074becbf43"}}
+TRAFFIC = {"k_force_f64": {"bytes": 47.05e6 + 62.96e6, "n": 2 ** 20, "src_sha": "01dc06074becbf43"},
+           # each pair once: per force evaluation (1 one-sided launch on the diagonal
+           # blocks + 128 x (pair launch + combine launch)), from the first launch of
+           # each kernel in one capture
+           "k_force_f64_sym": {"bytes": 34.22e6 + 128 * (703.07e6 + 589.66e6), "n": 2 ** 20,
+                               "src_sha": "67da7c2abed4b181"}}
 
 
 def _kernel_src_sha(names):
@@ -72,7 +77,14 @@ def _kernel_src_sha(names):
 
 def traffic_f64(n, sym=False):
     if sym:
-        return None
+        t = TRAFFIC["k_force_f64_sym"]
+        sha = _kernel_src_sha(["__device__ __forceinline__ void rsqrt_recip_sig(",
+                               "__device__ __forceinline__ uint64_t mul_sig(",
+                               "__device__ __forceinline__ void scale_pair(",
+                               "__device__ __forceinline__ void body_f64_sym(",
+                               "__global__ void __launch_bounds__(BT) k_force_f64_sym(",
+                               "__global__ void k_sym_combine("])
+        return t["bytes"] if (sha == t["src_sha"] and n == t["n"]) else None
     t = TRAFFIC["k_force_f64"]
     sha = _kernel_src_sha(["__device__ __forceinline__ void rsqrt_recip_sig(",
                            "__device__ __forceinline__ uint64_t mul_sig(",
@@ -379,9 +391,13 @@ def run_gpu(args):
                      "achieved": achieved_tf,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
                      "traffic": traffic_f64(n, sym),
-                     "traffic_note": "DRAM bytes per force evaluation from one full-size ncu capture; the "
-                                     "O(N) algorithmic bytes (32 B in + partial sums out per particle) "
-                                     "mostly stay in the 129 MB L2",
+                     "traffic_note": ("DRAM bytes per force evaluation from one full-size ncu capture: "
+                                      "mostly the per-diagonal row/column slices of the each-pair-once "
+                                      "schedule, O(N^2/512), far above the O(N) algorithmic bytes but "
+                                      "~0.2% of HBM bandwidth over the evaluation" if sym else
+                                      "DRAM bytes per force evaluation from one full-size ncu capture; the "
+                                      "O(N) algorithmic bytes (32 B in + partial sums out per particle) "
+                                      "mostly stay in the 129 MB L2"),
                      "flop_convention": f"{FLOP_PER_INTERACTION} flop/interaction x N^2 per force evaluation"
                                         + ("; each pair is evaluated once for both particles, so the "
                                            "convention can exceed the FP64 peak: fp64_pipe.frac is the "
@@ -496,6 +512,75 @@ def run_drift(args):
     print(json.dumps(out), flush=True)
 
 
+def run_evolution(args):
+    """The paper's SP-against-DP evolution diagnostics as data (Figs. 6-7): the
+    same disk + halo initial state integrated in each mode of --evolution; every
+    --evolution-every steps the deviation of the total momentum |P - P0| and of
+    the centre of mass |R_cm - R_cm0| (whole system and disk), and the disk's
+    surface density on a 128 x 128 grid over [-6, 6]^2 (mass per unit area of
+    the disk particles projected on the z = 0 plane).  Maps and curves go to
+    --evolution-out (npz); the JSON line summarises them against the first mode
+    listed (the reference).  A mode written with a trailing "~" starts from the
+    same state with one coordinate moved by one ulp: N-body dynamics is chaotic,
+    so this control shows how far any rounding difference alone carries."""
+    import torch
+    import nbody_ics
+    import paper_1803_01190_gb300 as nb
+    modes = args.evolution.split(",")
+    w = nbody_ics.workload("disk_halo", n=args.n)
+    nd = args.n // 2                   # disk particles come first
+    edges = np.linspace(-6.0, 6.0, 129)
+    area = (edges[1] - edges[0]) ** 2
+    data, summary = {}, {}
+    for mode in modes:
+        times, com, com_disk, dP, maps = [], [], [], [], []
+        pos0 = w["pos"].copy()
+        if mode.endswith("~"):
+            pos0[0, 0] = np.nextafter(pos0[0, 0], np.inf)
+        with nb.Simulation(args.n, mode=mode.rstrip("~"), eps=EPS) as sim:
+            sim.set_state(pos0, w["vel"], w["mass"])
+            P0 = sim.diagnostics()["P"]
+            done = 0
+            t0 = time.perf_counter()
+            while True:
+                pos, vel, t, _ = sim.get_state()
+                m = w["mass"]
+                times.append(t)
+                com.append((m[:, None] * pos).sum(0) / m.sum())
+                com_disk.append((m[:nd, None] * pos[:nd]).sum(0) / m[:nd].sum())
+                dP.append(float(np.linalg.norm(sim.diagnostics()["P"] - P0)))
+                h, _, _ = np.histogram2d(pos[:nd, 0], pos[:nd, 1], bins=[edges, edges], weights=m[:nd])
+                maps.append(h / area)
+                if done >= args.evolution_steps:
+                    break
+                k = min(args.evolution_every, args.evolution_steps - done)
+                sim.step(DT, k)
+                done += k
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        com, com_disk, maps = np.array(com), np.array(com_disk), np.array(maps)
+        data.update({f"{mode}_t": np.array(times), f"{mode}_com": com, f"{mode}_com_disk": com_disk,
+                     f"{mode}_dP": np.array(dP), f"{mode}_sigma": maps})
+        summary[mode] = {"wall_s": wall,
+                         "max_dP_abs": float(max(dP)),
+                         "max_dRcm": float(np.linalg.norm(com - com[0], axis=1).max()),
+                         "max_dRcm_disk": float(np.linalg.norm(com_disk - com_disk[0], axis=1).max())}
+    ref = modes[0]
+    for mode in modes[1:]:
+        a, b = data[f"{ref}_sigma"], data[f"{mode}_sigma"]
+        summary[mode]["sigma_L1_diff_vs_" + ref] = [
+            float(np.abs(a[k] - b[k]).sum() / a[k].sum()) for k in range(len(a))]
+        summary[mode]["sigma_max_abs_diff_vs_" + ref] = [float(np.abs(a[k] - b[k]).max())
+                                                         for k in range(len(a))]
+    summary["times"] = data[f"{ref}_t"].tolist()
+    if args.evolution_out:
+        np.savez_compressed(args.evolution_out, edges=edges, **data)
+    print(json.dumps({"evolution": modes, "n": args.n, "eps": EPS, "dt": DT,
+                      "steps": args.evolution_steps, "every": args.evolution_every,
+                      "workload": workload_desc(args.n), "out": args.evolution_out,
+                      "summary": summary}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -512,6 +597,11 @@ def main():
                     help="long conservation run of the workload in this mode (Table 2 quantities)")
     ap.add_argument("--drift-steps", type=int, default=10000)
     ap.add_argument("--drift-scheme", choices=["kdk", "fr4", "rk4"], default="kdk")
+    ap.add_argument("--evolution", default=None,
+                    help="comma-separated modes, the first the reference: SP-against-DP evolution data")
+    ap.add_argument("--evolution-steps", type=int, default=20000)
+    ap.add_argument("--evolution-every", type=int, default=2000)
+    ap.add_argument("--evolution-out", default=None, help="npz file for the maps and curves")
     ap.add_argument("--drift-dt", type=float, default=DT)
     ap.add_argument("--drift-every", type=int, default=100)
     ap.add_argument("--profile-force", choices=["fp64", "f64e", "mixed", "fp32"], default=None,
@@ -521,6 +611,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.drift:
         run_drift(args)
+    elif args.evolution:
+        run_evolution(args)
     elif args.profile_force:
         profile_force(args)
     elif args.impl == "reference":
