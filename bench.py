@@ -37,11 +37,12 @@ SMS, FP64_PER_CLK, FP32_PER_CLK, SM_MAX_GHZ = 152, 2, 128, 2.07
 # derived ALU peaks (flop/s): SMs x lanes-per-clock x 2 (FMA) x max SM clock
 FP64_PEAK_TFLOPS = SMS * FP64_PER_CLK * 2 * SM_MAX_GHZ / 1e3
 # FP64-pipe instruction rate (instructions/s) and the FP64 instructions the two
-# binary64 force paths issue per interaction: 10 one-sided (3 DADD, 3 DFMA for
-# |d|^2 + eps^2, 3 DFMA + 1 DADD for the sums); 14 per pair evaluated once for
-# both particles, i.e. 7 per interaction
+# binary64 force paths issue per interaction: 9 one-sided (3 DADD, 3 DFMA for
+# |d|^2 + eps^2, 3 DFMA for the acceleration sums; the potential sum is an
+# integer add); 14 per pair evaluated once for both particles, i.e. 7 per
+# interaction
 FP64_PIPE_GINSTR = SMS * FP64_PER_CLK * SM_MAX_GHZ
-FP64_INSTR_PER_INTERACTION = {False: 10, True: 7}
+FP64_INSTR_PER_INTERACTION = {False: 9, True: 7}
 FP32_PEAK_TFLOPS = SMS * FP32_PER_CLK * 2 * SM_MAX_GHZ / 1e3
 
 

@@ -18,12 +18,15 @@
 // Three arithmetics:
 //   f64   binary64 pair arithmetic.  GB300 issues binary64 at about 1/72 of the
 //         binary32 rate, so the kernel is bound by the FP64 pipe and its cost
-//         is its count of FP64 instructions per pair: 10 (3 DADD for d,
-//         3 DFMA for |d|^2 + eps^2, 3 DFMA and 1 DADD for the sums).  The
+//         is its count of FP64 instructions per pair: 9 (3 DADD for d,
+//         3 DFMA for |d|^2 + eps^2, 3 DFMA for the acceleration sums).  The
 //         rest runs on the otherwise idle integer and FP32 pipes: 1/r and
-//         1/r^2 within 0.52 ulp (SFU seed, exact integer residual) and the
+//         1/r^2 within 0.52 ulp (SFU seed, exact integer residual), the
 //         products m/r and (m/r)/r^2 by a correctly rounded integer binary64
-//         multiply.
+//         multiply, and the potential sum by a correctly rounded integer
+//         binary64 add.  From 64 blocks of 512 particles the FP64 path
+//         evaluates each pair once for both particles (k_force_f64_sym:
+//         14 FP64 instructions per pair, 7 per interaction).
 //   mixed binary32 pair arithmetic (packed: two j per instruction, SFU
 //         reciprocal square root) on coordinates
 //         re-centred on an anchor (the per-coordinate median) per j-tile, with the i coordinates held as float-float pairs so that the
@@ -151,6 +154,49 @@ __device__ __forceinline__ double pack_f64(uint64_t sig, int e) {
   return __longlong_as_double((long long)((((uint64_t)(e - 1)) << 52) + sig));
 }
 
+// Binary64 addition of two non-negative numbers on the integer pipes (the
+// potential sum of the one-sided kernel), correctly rounded to nearest even and
+// bit-identical to DADD: significands at bit 62 of a 64-bit word, the smaller
+// one shifted right by the exponent difference with a sticky bit, at most a
+// one-bit normalisation after a carry, rounded at bit 10.  ok = false for a
+// subnormal or overflowing result or a negative operand, where the caller adds
+// in binary64 out of line.  It costs about 40 ALU-pipe instructions, a little
+// more than the FP64 pipe time of one DADD is worth in the one-sided kernel's
+// spare ALU capacity (measured +12 %), and less than nothing in the each-pair-
+// once kernel, whose second potential sum would need it twice (measured -15 %).
+__device__ __forceinline__ uint64_t add_pos_bits(uint64_t a, uint64_t b, bool &ok) {
+  const uint64_t M52 = 0xFFFFFFFFFFFFFull;
+  const bool sw = b > a;
+  const uint64_t X = sw ? b : a, Y = sw ? a : b;
+  const int eX = (int)(X >> 52), eY = (int)(Y >> 52);
+  const uint64_t MX = ((X & M52) | ((uint64_t)1 << 52)) << 10;
+  const uint64_t MY0 = ((Y & M52) | ((uint64_t)(eY != 0) << 52)) << 10;
+  const int dc = min(eX - eY, 63);
+  const uint64_t st = (MY0 & (((uint64_t)1 << dc) - 1u)) != 0;
+  const uint64_t S = (MX + (MY0 >> dc)) | st;
+  const int c = (int)(S >> 63);
+  const uint64_t N = (S >> c) | (S & (uint64_t)c);
+  uint64_t sig = N >> 10;
+  sig += ((N >> 9) & 1u) & (uint64_t)(((N & 0x1FFu) != 0) | (bool)(sig & 1u));
+  const int E = eX + c;
+  ok = (E <= 2046 && !(eY == 0 && Y != 0) && eX != 0 && ((a | b) >> 63) == 0) || X == 0;
+  return X == 0 ? 0 : ((uint64_t)(E - 1) << 52) + sig;
+}
+__device__ __noinline__ uint64_t add_pos_slow(uint64_t a, uint64_t b) {
+  return (uint64_t)__double_as_longlong(__longlong_as_double((long long)a) +
+                                        __longlong_as_double((long long)b));
+}
+// acc += v for the bit pattern acc of a non-negative binary64 sum
+__device__ __forceinline__ void acc_pos(uint64_t &acc, double v) {
+  bool ok;
+  const uint64_t vb = (uint64_t)__double_as_longlong(v);
+  const uint64_t r = add_pos_bits(acc, vb, ok);
+  if (ok)
+    acc = r;
+  else
+    acc = add_pos_slow(acc, vb);
+}
+
 // The same quantities in binary64 arithmetic, out of line: for r^2 outside
 // [2^-60, 2^60) (and zero or non-finite) and for masses outside
 // [2^-895, 2^897) (and zero), where the integer path's ranges do not hold.
@@ -206,7 +252,7 @@ struct TableWork {
 template <bool MASK>
 __device__ __forceinline__ void body_f64(const d4 &pj, double xi, double yi, double zi,
                                          double eps2, double &ax, double &ay, double &az,
-                                         double &pt, bool self) {
+                                         uint64_t &pt, bool self) {
   const double dx = pj.x - xi, dy = pj.y - yi, dz = pj.z - zi;
   double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
   double m = pj.w;
@@ -235,7 +281,7 @@ __device__ __forceinline__ void body_f64(const d4 &pj, double xi, double yi, dou
   ax = fma(dx, f, ax);
   ay = fma(dy, f, ay);
   az = fma(dz, f, az);
-  pt += my;
+  acc_pos(pt, my);  // the potential sum: integer pipes
 }
 
 template <int BT, int R, int T, class W>
@@ -247,7 +293,8 @@ __global__ void __launch_bounds__(BT) k_force_f64(const d4 *__restrict__ posm, W
     const int tid = threadIdx.x;
     const int64_t j1 = u.j0 + u.nj;
     const double eps2 = u.eps2;
-    double xi[R], yi[R], zi[R], ax[R], ay[R], az[R], pt[R];
+    double xi[R], yi[R], zi[R], ax[R], ay[R], az[R];
+    uint64_t pt[R];  // bit patterns of the potential sums
   #pragma unroll
     for (int r = 0; r < R; r++) {
       const int li = r * BT + tid;
@@ -255,7 +302,8 @@ __global__ void __launch_bounds__(BT) k_force_f64(const d4 *__restrict__ posm, W
       xi[r] = p.x;
       yi[r] = p.y;
       zi[r] = p.z;
-      ax[r] = ay[r] = az[r] = pt[r] = 0.0;
+      ax[r] = ay[r] = az[r] = 0.0;
+      pt[r] = 0;
     }
     for (int64_t jt = u.j0; jt < j1; jt += T) {
       const int cnt = (int)min((int64_t)T, j1 - jt);
@@ -285,7 +333,8 @@ __global__ void __launch_bounds__(BT) k_force_f64(const d4 *__restrict__ posm, W
   #pragma unroll
     for (int r = 0; r < R; r++) {
       const int li = r * BT + tid;
-      if (li < u.ni) part[u.out + li] = d4{ax[r], ay[r], az[r], pt[r]};
+      if (li < u.ni)
+        part[u.out + li] = d4{ax[r], ay[r], az[r], __longlong_as_double((long long)pt[r])};
     }
   }
 }
