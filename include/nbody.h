@@ -187,14 +187,14 @@ int nbody_set_launch(nbody_ctx *ctx, int ipt, int jsplit);
 int nbody_get_launch(nbody_ctx *ctx, int *ipt, int *jsplit, int *threads, int *tile);
 
 /*
- * FP64 mode only: evaluate each unordered pair once and apply it to both
- * particles (Newton's third law; the same binary64 terms with opposite signs,
- * summed in a different fixed order than the one-sided kernel, so results
- * differ from it by rounding only and stay deterministic).  mode = -1 (default):
- * automatic, used when n spans at least 64 blocks of 512 particles; 0: never;
- * 1: whenever n spans at least 2 blocks.  The launch shape of nbody_set_launch
- * does not apply to this path.
- * Errors: EINVAL (NULL context, mode outside -1..1, mode 1 outside FP64).
+ * FP64 and F64E modes: evaluate each unordered pair once and apply it to both
+ * particles (Newton's third law; the same terms with opposite signs, summed in
+ * a different fixed order than the one-sided kernels, so results differ from
+ * them by rounding only and stay deterministic).  Particles are cut into
+ * blocks of 512 (FP64) or 256 (F64E).  mode = -1 (default): automatic, used
+ * when n spans at least 64 blocks; 0: never; 1: whenever n spans at least 2
+ * blocks.  The launch shape of nbody_set_launch does not apply to this path.
+ * Errors: EINVAL (NULL context, mode outside -1..1, mode 1 in MIXED or FP32).
  */
 int nbody_set_symmetric(nbody_ctx *ctx, int mode);
 /* The setting (-1, 0, 1) and whether the next force evaluation uses the path. */

@@ -148,22 +148,27 @@ static int ensure_part(nbody_ctx *c, int S) {
 // N = 2^14; 68.5 against 56.6 at 64 blocks, N = 2^15).
 static const int SYM_AUTO_MIN_BLOCKS = 64;
 
+static int sym_block(const nbody_ctx *c) {
+  return c->mode == NBODY_F64E ? nb::sym_block_particles_ff() : nb::sym_block_particles();
+}
+
 static int sym_blocks(const nbody_ctx *c) {
-  const int B = nb::sym_block_particles();
+  const int B = sym_block(c);
   return (int)((c->n + B - 1) / B);
 }
 
 static bool use_sym(const nbody_ctx *c) {
-  if (c->mode != NBODY_FP64 || c->sym == 0) return false;
+  if ((c->mode != NBODY_FP64 && c->mode != NBODY_F64E) || c->sym == 0) return false;
   return c->sym == 1 ? sym_blocks(c) >= 2 : sym_blocks(c) >= SYM_AUTO_MIN_BLOCKS;
 }
 
-// FP64, each pair once: slice 0 of c->part = pairs inside each block (the
-// one-sided kernel on the M diagonal blocks), slice 1 = row sums and slice 2 =
-// column sums of the M (M - 1) / 2 pairs of distinct blocks, added over the
-// block diagonals in order.
+// FP64 and F64E, each pair once: slice 0 of c->part = pairs inside each block
+// (the one-sided kernel on the M diagonal blocks), slice 1 = row sums and
+// slice 2 = column sums of the M (M - 1) / 2 pairs of distinct blocks, added
+// over the block diagonals in order.  F64E blocks are its float-float tiles.
 static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
-  const int B = nb::sym_block_particles();
+  const bool ff = c->mode == NBODY_F64E;
+  const int B = sym_block(c);
   const int M = sym_blocks(c);
   const int nd = M / 2;
   int rc = ensure_part(c, 3);
@@ -176,7 +181,7 @@ static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
     for (int I = 0; I < M; I++) {
       u[I].i0 = u[I].j0 = u[I].out = (int64_t)I * B;
       u[I].ni = u[I].nj = (int32_t)std::min<int64_t>(B, c->n - (int64_t)I * B);
-      u[I].anchor = 0;
+      u[I].anchor = ff ? I : 0;  // F64E: block I is float-float tile I
       u[I].eps2 = c->eps * c->eps;
     }
     if (cudaMalloc(&c->sym_units, sizeof(nb::Unit) * M) != cudaSuccess)
@@ -186,7 +191,8 @@ static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
   }
   if (!c->sym_d && nd > 0) {
     // enough work items per launch for ~32 waves, within 1 GiB of buffers
-    const int64_t slots = (int64_t)c->num_sms * std::max(1, nb::sym_blocks_per_sm());
+    const int per_sm = ff ? nb::sym_blocks_per_sm_ff() : nb::sym_blocks_per_sm();
+    const int64_t slots = (int64_t)c->num_sms * std::max(1, per_sm);
     int64_t D = (32 * slots + M - 1) / M;
     const int64_t cap = std::max<int64_t>(1, ((int64_t)1 << 30) / (64 * c->n));
     D = std::max<int64_t>(1, std::min<int64_t>({D, cap, (int64_t)nd}));
@@ -194,8 +200,13 @@ static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
       return fail(NBODY_ENOMEM, "row/column buffers");
     c->sym_d = (int)D;
   }
-  CK(nb::launch_force_units(NBODY_FP64, posm_in, nullptr, nullptr, c->sym_units, M, nb::sym_r(),
-                            c->part, 0, c->st));
+  if (ff) {
+    CK(nb::launch_mixed_prep((const nb::d4 *)posm_in, c->n, nb::force_tile(NBODY_F64E), c->fpos,
+                             c->anchor, c->st, true));
+    c->launches++;
+  }
+  CK(nb::launch_force_units(c->mode, posm_in, c->fpos, c->anchor, c->sym_units, M,
+                            ff ? nb::sym_r_ff() : nb::sym_r(), c->part, 0, c->st));
   c->launches++;
   S = 1;
   if (nd == 0) return NBODY_OK;
@@ -203,8 +214,12 @@ static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
   nb::d4 *rows = (nb::d4 *)c->sym_buf, *cols = rows + (int64_t)c->sym_d * c->n;
   for (int d0 = 1; d0 <= nd; d0 += c->sym_d) {
     const int D = std::min(c->sym_d, nd - d0 + 1);
-    CK(nb::launch_force_f64_sym((const nb::d4 *)posm_in, c->n, c->eps * c->eps, M, d0, D, rows,
-                                cols, c->st));
+    if (ff)
+      CK(nb::launch_force_f64e_sym((const nb::d4 *)posm_in, c->fpos, c->anchor, c->n,
+                                   c->eps * c->eps, M, d0, D, rows, cols, c->st));
+    else
+      CK(nb::launch_force_f64_sym((const nb::d4 *)posm_in, c->n, c->eps * c->eps, M, d0, D, rows,
+                                  cols, c->st));
     CK(nb::launch_sym_combine(rows, cols, D, c->n, part + c->n, part + 2 * c->n, d0 == 1, c->st));
     c->launches += 2;
   }
@@ -651,7 +666,8 @@ int nbody_get_launch(nbody_ctx *c, int *ipt, int *jsplit, int *threads, int *til
 int nbody_set_symmetric(nbody_ctx *c, int mode) {
   if (!c) return fail(NBODY_EINVAL, "NULL context");
   if (mode < -1 || mode > 1) return fail(NBODY_EINVAL, "symmetric mode must be -1, 0 or 1");
-  if (mode == 1 && c->mode != NBODY_FP64) return fail(NBODY_EINVAL, "each-pair-once path is FP64 only");
+  if (mode == 1 && c->mode != NBODY_FP64 && c->mode != NBODY_F64E)
+    return fail(NBODY_EINVAL, "each-pair-once path is FP64 and F64E only");
   c->sym = mode;
   return NBODY_OK;
 }

@@ -837,6 +837,211 @@ __global__ void __launch_bounds__(BT) k_force_f64e(const d4 *__restrict__ posm,
   }
 }
 
+// ---------------------------------------------------------------- float-float, each pair once
+// The F64E pair body evaluated once for both particles (Newton's third law):
+// the difference, |d|^2 + eps^2, y = 1/r and q = y^2 are shared; the i side
+// gets m_j y and m_j y q, the j side m_i y and m_i y q with -d.  Two
+// j-particles per packed instruction (one tile entry); the j side's four
+// float-float sums for an entry are (gh, gl).
+__device__ __forceinline__ void body_ff_sym(const float4 &H, const float4 &H2, const float4 &L,
+                                            const float4 &L2, float2 nxh, float2 nxl,
+                                            float2 nyh, float2 nyl, float2 nzh, float2 nzl,
+                                            float2 mih, float2 mil, float2 e2h, float2 e2l,
+                                            float2 (&ah)[4], float2 (&al)[4], float2 (&gh)[4],
+                                            float2 (&gl)[4]) {
+  float2 dh[3], dl[3];
+  {
+    const float2 jh[3] = {f2(H.x, H.y), f2(H.z, H.w), f2(H2.x, H2.y)};
+    const float2 jl[3] = {f2(L.x, L.y), f2(L.z, L.w), f2(L2.x, L2.y)};
+    const float2 ih[3] = {nxh, nyh, nzh}, il[3] = {nxl, nyl, nzl};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {  // d = (jh + jl) - (ih + il), renormalised
+      float2 s, e;
+      two_sum2(jh[c], ih[c], s, e);
+      const float2 t = __fadd2_rn(__fadd2_rn(jl[c], il[c]), e);
+      two_sum2(s, t, dh[c], dl[c]);
+    }
+  }
+  float2 p[3], pe[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    two_prod2(dh[c], dh[c], p[c], pe[c]);
+    pe[c] = __ffma2_rn(__fadd2_rn(dh[c], dh[c]), dl[c], pe[c]);
+  }
+  float2 s1, e1, s2, e2, s3, e3;
+  two_sum2(p[0], p[1], s1, e1);
+  two_sum2(s1, p[2], s2, e2);
+  two_sum2(s2, e2h, s3, e3);
+  const float2 lo = __fadd2_rn(__fadd2_rn(__fadd2_rn(pe[0], pe[1]), __fadd2_rn(pe[2], e2l)),
+                               __fadd2_rn(__fadd2_rn(e1, e2), e3));
+  float2 r2h, r2l;
+  fast_two_sum2(s3, lo, r2h, r2l);
+  const float2 y0 = f2(rsqrt_approx(r2h.x), rsqrt_approx(r2h.y));
+  float2 th, tl, u, ue;
+  two_prod2(y0, y0, th, tl);
+  two_prod2(r2h, th, u, ue);
+  const float2 cross = __ffma2_rn(r2h, tl, __fmul2_rn(r2l, th));
+  const float2 e = fsub2(fsub2(fsub2(f2(1.0f, 1.0f), u), ue), cross);
+  const float2 yl = __fmul2_rn(__fmul2_rn(y0, e), __ffma2_rn(e, f2(0.375f, 0.375f), f2(0.5f, 0.5f)));
+  float2 q, qe;
+  two_prod2(y0, y0, q, qe);
+  const float2 ql = __ffma2_rn(__fadd2_rn(y0, y0), yl, qe);
+  // one side: a = m y, b = a q, sums += (sgn d b, a)
+  auto side = [&](float2 mh, float2 ml, bool neg, float2(&sh)[4], float2(&sl)[4]) {
+    float2 a, ae, b, be;
+    two_prod2(mh, y0, a, ae);
+    const float2 al_ = __ffma2_rn(mh, yl, __ffma2_rn(ml, y0, ae));
+    two_prod2(a, q, b, be);
+    const float2 bl = __ffma2_rn(a, ql, __ffma2_rn(al_, q, be));
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      float2 th2, tl2;
+      if (c < 3) {
+        const float2 dhc = neg ? neg2(dh[c]) : dh[c], dlc = neg ? neg2(dl[c]) : dl[c];
+        float2 ce;
+        two_prod2(dhc, b, th2, ce);
+        tl2 = __ffma2_rn(dhc, bl, __ffma2_rn(dlc, b, ce));
+      } else {
+        th2 = a;
+        tl2 = al_;
+      }
+      float2 s, es;
+      two_sum2(sh[c], th2, s, es);
+      fast_two_sum2(s, __fadd2_rn(sl[c], __fadd2_rn(es, tl2)), sh[c], sl[c]);
+    }
+  };
+  side(f2(H2.z, H2.w), f2(L2.z, L2.w), false, ah, al);
+  side(mih, mil, true, gh, gl);
+}
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+  return f2(__shfl_sync(0xFFFFFFFFu, v.x, src), __shfl_sync(0xFFFFFFFFu, v.y, src));
+}
+
+// Work item (d, I) of the block-diagonal schedule of k_force_f64_sym with
+// blocks of B = BT*R = T particles: one F64E tile (one anchor) per column
+// block.  Row sums into rows[dl], column sums into cols[dl], binary64.
+template <int BT, int R, int T>
+__global__ void __launch_bounds__(BT) k_force_f64e_sym(const d4 *__restrict__ posm,
+                                                       const float4 *__restrict__ jff,
+                                                       const float4 *__restrict__ anchor,
+                                                       int64_t n, double eps2, int M, int d0,
+                                                       d4 *__restrict__ rows,
+                                                       d4 *__restrict__ cols) {
+  constexpr int B = BT * R, NW = BT / 32, NE = T / 2;  // NE tile entries of 2 j
+  static_assert(B == T && NE == BT, "one tile per block, one column entry per thread");
+  __shared__ float4 tH[NE], tH2[NE], tL[NE], tL2[NE];
+  __shared__ double colw[NW][4][T];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int dl = blockIdx.x / M, I = blockIdx.x % M, d = d0 + dl;
+  const int J = (I + d) % M;
+  const int64_t i0 = (int64_t)I * B, j0 = (int64_t)J * B;
+  d4 *rowo = rows + (int64_t)dl * n;
+  d4 *colo = cols + (int64_t)dl * n;
+  if (2 * d == M && I >= M / 2) {
+    for (int k = tid; k < B; k += BT) {
+      if (i0 + k < n) rowo[i0 + k] = d4{0.0, 0.0, 0.0, 0.0};
+      if (j0 + k < n) colo[j0 + k] = d4{0.0, 0.0, 0.0, 0.0};
+    }
+    return;
+  }
+  const float e2hs = (float)eps2;
+  const float e2ls = (float)(eps2 - (double)e2hs);
+  const float2 e2h = f2(e2hs, e2hs), e2l = f2(e2ls, e2ls);
+  {  // entry tid = j0 + 2 tid, j0 + 2 tid + 1; beyond n massless at 1e18 from the anchor
+    const int64_t ja = j0 + 2 * tid, jb = ja + 1;
+    const float4 dh = make_float4(1e18f, 1e18f, 1e18f, 0.0f), dz = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const float4 ah_ = ja < n ? jff[2 * ja] : dh, alo = ja < n ? jff[2 * ja + 1] : dz;
+    const float4 bh_ = jb < n ? jff[2 * jb] : dh, blo = jb < n ? jff[2 * jb + 1] : dz;
+    tH[tid] = make_float4(ah_.x, bh_.x, ah_.y, bh_.y);
+    tH2[tid] = make_float4(ah_.z, bh_.z, ah_.w, bh_.w);
+    tL[tid] = make_float4(alo.x, blo.x, alo.y, blo.y);
+    tL2[tid] = make_float4(alo.z, blo.z, alo.w, blo.w);
+  }
+  const float4 ch = anchor[2 * J], cl = anchor[2 * J + 1];
+  const float chv[3] = {ch.x, ch.y, ch.z}, clv[3] = {cl.x, cl.y, cl.z};
+  float2 nh[R][3], nl[R][3], ah[R][4], al[R][4], mh[R], ml[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const int64_t i = i0 + r * BT + tid;
+    // beyond n: massless, 1e18 from the anchor (finite r^2, zero contribution)
+    const d4 pi = i < n ? posm[i] : d4{0.0, 0.0, 0.0, 0.0};
+    const double c3[3] = {pi.x, pi.y, pi.z};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {  // -(x_i - c_J) as float-float
+      const float xh = __double2float_rn(c3[c]);
+      const float xl = __double2float_rn(c3[c] - (double)xh);
+      float s, e;
+      two_sum1(xh, -chv[c], s, e);
+      const float t = __fadd_rn(__fsub_rn(xl, clv[c]), e);
+      float h, l;
+      two_sum1(s, t, h, l);
+      if (i >= n) h = 1e18f, l = 0.0f;
+      nh[r][c] = f2(-h, -h);
+      nl[r][c] = f2(-l, -l);
+    }
+    const float m_h = __double2float_rn(pi.w);
+    const float m_l = __double2float_rn(pi.w - (double)m_h);
+    mh[r] = f2(m_h, m_h);
+    ml[r] = f2(m_l, m_l);
+#pragma unroll
+    for (int c = 0; c < 4; c++) ah[r][c] = al[r][c] = f2(0.0f, 0.0f);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int c0 = 0; c0 < NE; c0 += 32) {
+    float2 gh[4], gl[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) gh[c] = gl[c] = f2(0.0f, 0.0f);
+#pragma unroll 1
+    for (int k = 0; k < 32; k++) {
+      const int ent = c0 + ((lane + k) & 31);
+      const float4 H = tH[ent], H2 = tH2[ent], L = tL[ent], L2 = tL2[ent];
+#pragma unroll
+      for (int r = 0; r < R; r++)
+        body_ff_sym(H, H2, L, L2, nh[r][0], nl[r][0], nh[r][1], nl[r][1], nh[r][2], nl[r][2],
+                    mh[r], ml[r], e2h, e2l, ah[r], al[r], gh, gl);
+      const int src = (lane + 1) & 31;
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        gh[c] = shfl2(gh[c], src);
+        gl[c] = shfl2(gl[c], src);
+      }
+    }
+    // lane holds entry c0 + lane (j = 2 (c0 + lane) and 2 (c0 + lane) + 1)
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      colw[warp][c][2 * (c0 + lane)] = f2d_exact(gh[c].x) + f2d_exact(gl[c].x);
+      colw[warp][c][2 * (c0 + lane) + 1] = f2d_exact(gh[c].y) + f2d_exact(gl[c].y);
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < T; k += BT) {
+    double v[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      v[c] = colw[0][c][k];
+#pragma unroll
+      for (int w = 1; w < NW; w++) v[c] += colw[w][c][k];
+    }
+    if (j0 + k < n) colo[j0 + k] = d4{v[0], v[1], v[2], v[3]};
+  }
+  // rows: fold even + odd lanes in float-float, then into binary64
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const int64_t i = i0 + r * BT + tid;
+    double v[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      float s, e;
+      two_sum1(ah[r][c].x, ah[r][c].y, s, e);
+      const float l = __fadd_rn(__fadd_rn(al[r][c].x, al[r][c].y), e);
+      v[c] = f2d_exact(s) + f2d_exact(l);
+    }
+    if (i < n) rowo[i] = d4{v[0], v[1], v[2], v[3]};
+  }
+}
+
 // ---------------------------------------------------------------- mixed
 // fpos[j] = (x_j - c_t, y_j - c_t, z_j - c_t, m_j) in binary32, c_t the anchor of
 // j's tile; anchor[2t] = float hi part of c_t, anchor[2t+1] = float lo part.
@@ -1166,6 +1371,27 @@ int sym_blocks_per_sm() {
 cudaError_t launch_force_f64_sym(const d4 *posm, int64_t n, double eps2, int M, int d0, int D,
                                  d4 *rows, d4 *cols, cudaStream_t st) {
   k_force_f64_sym<SYM_BT, SYM_R, SYM_T><<<D * M, SYM_BT, 0, st>>>(posm, n, eps2, M, d0, rows, cols);
+  return cudaGetLastError();
+}
+
+constexpr int SYMFF_BT = 128, SYMFF_R = 2, SYMFF_T = 256;
+
+int sym_block_particles_ff() { return SYMFF_BT * SYMFF_R; }
+int sym_r_ff() { return SYMFF_R; }
+
+int sym_blocks_per_sm_ff() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &nb, k_force_f64e_sym<SYMFF_BT, SYMFF_R, SYMFF_T>, SYMFF_BT, 0) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+cudaError_t launch_force_f64e_sym(const d4 *posm, const float4 *jff, const float4 *anchor,
+                                  int64_t n, double eps2, int M, int d0, int D, d4 *rows,
+                                  d4 *cols, cudaStream_t st) {
+  k_force_f64e_sym<SYMFF_BT, SYMFF_R, SYMFF_T><<<D * M, SYMFF_BT, 0, st>>>(
+      posm, jff, anchor, n, eps2, M, d0, rows, cols);
   return cudaGetLastError();
 }
 

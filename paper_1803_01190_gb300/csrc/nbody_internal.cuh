@@ -104,6 +104,14 @@ cudaError_t launch_force_f64_sym(const d4 *posm, int64_t n, double eps2, int M, 
                                  d4 *rows, d4 *cols, cudaStream_t st);
 cudaError_t launch_sym_combine(const d4 *rows, const d4 *cols, int D, int64_t n, d4 *acc_rows,
                                d4 *acc_cols, bool first, cudaStream_t st);
+// F64E, each pair once: blocks of sym_block_particles_ff() particles (one
+// float-float tile each); jff / anchor from launch_mixed_prep(..., ff = true)
+int sym_block_particles_ff();
+int sym_r_ff();
+int sym_blocks_per_sm_ff();
+cudaError_t launch_force_f64e_sym(const d4 *posm, const float4 *jff, const float4 *anchor,
+                                  int64_t n, double eps2, int M, int d0, int D, d4 *rows,
+                                  d4 *cols, cudaStream_t st);
 
 bool shape_supported(int mode, const Shape &sh);
 

@@ -140,6 +140,44 @@ def test_fp64_symmetric_accel_sizes(nb, n, eps):
     _check_fp64(acc, pot, pos, mass, eps, 1.3)
 
 
+# F64E: 256-particle blocks (one float-float tile each): n = 257, 512 (M = 2), 700 (M = 3),
+# 1025 (M = 5, tail of 1), 2303 (M = 9, odd tail)
+@pytest.mark.parametrize("n", [257, 512, 700, 1025, 2303])
+@pytest.mark.parametrize("eps", [0.01, 0.0])
+def test_f64e_symmetric_accel_sizes(nb, n, eps):
+    pos, _, _ = nbody_ics.plummer(n, 41 + n)
+    mass = nbody_ics.lognormal_masses(n, 42 + n)
+    with nb.Simulation(n, "f64e", eps=eps, G=0.7) as sim:
+        sim.set_symmetric(1)
+        assert sim.get_symmetric() == (1, True)
+        acc, pot = sim.accel(pos, mass)
+    _check_fp64(acc, pot, pos, mass, eps, 0.7)
+
+
+def test_f64e_symmetric_against_one_sided_and_kdk(nb):
+    n = 6000
+    w = nbody_ics.workload("disk_halo", n=n)
+    mass = w["mass"].copy()
+    mass[::9] = 0.0
+    with nb.Simulation(n, "f64e", eps=w["eps"]) as sim:
+        sim.set_symmetric(1)
+        acc_s, pot_s = sim.accel(w["pos"], mass)
+        acc_s2, _ = sim.accel(w["pos"], mass)
+        sim.set_symmetric(0)
+        acc_o, pot_o = sim.accel(w["pos"], mass)
+        sim.set_symmetric(1)
+        sim.set_state(w["pos"], w["vel"], mass)
+        sim.step(5e-4, 3)
+        p, v, _, _ = sim.get_state()
+    assert np.array_equal(acc_s, acc_s2)
+    rows = np.arange(0, n, 37)
+    _check_fp64(acc_s, pot_s, w["pos"], mass, w["eps"], rows=rows)
+    _check_fp64(acc_o, pot_o, w["pos"], mass, w["eps"], rows=rows)
+    op, ov, _, _ = oracle.kdk(w["pos"], w["vel"], mass, w["eps"], 1.0, 5e-4, 3)
+    assert np.abs(p - op).max() <= 1e-12 * np.abs(op).max()
+    assert np.abs(v - ov).max() <= 1e-11 * np.abs(ov).max()
+
+
 def test_fp64_symmetric_auto_and_off(nb):
     w = nbody_ics.workload("disk_halo", n=40000)
     with nb.Simulation(40000, "fp64", eps=w["eps"]) as sim:
