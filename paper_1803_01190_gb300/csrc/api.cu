@@ -162,32 +162,47 @@ static bool use_sym(const nbody_ctx *c) {
   return c->sym == 1 ? sym_blocks(c) >= 2 : sym_blocks(c) >= SYM_AUTO_MIN_BLOCKS;
 }
 
-// FP64 and F64E, each pair once: slice 0 of c->part = pairs inside each block
-// (the one-sided kernel on the M diagonal blocks), slice 1 = row sums and
-// slice 2 = column sums of the M (M - 1) / 2 pairs of distinct blocks, added
-// over the block diagonals in order.  F64E blocks are its float-float tiles.
+// FP64 and F64E, each pair once: slices 0..P-1 of c->part = pairs inside each
+// block (the one-sided kernel on the M diagonal blocks, each block's j range in
+// P parts), slice P = row sums and slice P+1 = column sums of the M (M - 1) / 2
+// pairs of distinct blocks, added over the block diagonals in order.  F64E
+// blocks are its float-float tiles.
 static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
   const bool ff = c->mode == NBODY_F64E;
   const int B = sym_block(c);
   const int M = sym_blocks(c);
   const int nd = M / 2;
-  int rc = ensure_part(c, 3);
+  // pairs inside the diagonal blocks: each block's j range in P parts (one
+  // unit each, partial sums in slices 0..P-1) so that the one-sided launch has
+  // at least two work items per resident block slot
+  const int per_sm_1 = nb::force_max_blocks_per_sm(c->mode, nb::Shape{nb::force_block_threads(c->mode),
+                                                                      ff ? nb::sym_r_ff() : nb::sym_r(),
+                                                                      nb::force_tile(c->mode), 1});
+  const int64_t slots_1 = (int64_t)c->num_sms * std::max(1, per_sm_1);
+  const int P = (int)std::max<int64_t>(1, std::min<int64_t>(ff ? 2 : 4, (2 * slots_1 + M - 1) / M));
+  int rc = ensure_part(c, P + 2);
   if (rc) return rc;
-  if (c->sym_units_m != M) {
+  if (c->sym_units_m != M * P) {
     if (c->sym_units) cudaFree(c->sym_units);
     c->sym_units = nullptr;
     c->sym_units_m = 0;
-    std::vector<nb::Unit> u((size_t)M);
-    for (int I = 0; I < M; I++) {
-      u[I].i0 = u[I].j0 = u[I].out = (int64_t)I * B;
-      u[I].ni = u[I].nj = (int32_t)std::min<int64_t>(B, c->n - (int64_t)I * B);
-      u[I].anchor = ff ? I : 0;  // F64E: block I is float-float tile I
-      u[I].eps2 = c->eps * c->eps;
-    }
-    if (cudaMalloc(&c->sym_units, sizeof(nb::Unit) * M) != cudaSuccess)
+    std::vector<nb::Unit> u((size_t)M * P);
+    const int64_t len = B / P;
+    for (int I = 0; I < M; I++)
+      for (int q = 0; q < P; q++) {
+        nb::Unit &v = u[(size_t)q * M + I];
+        v.i0 = (int64_t)I * B;
+        v.ni = (int32_t)std::min<int64_t>(B, c->n - v.i0);
+        v.j0 = v.i0 + q * len;
+        v.nj = (int32_t)std::max<int64_t>(0, std::min<int64_t>(len, c->n - v.j0));
+        v.out = (int64_t)q * c->n + v.i0;
+        v.anchor = ff ? I : 0;  // F64E: block I is float-float tile I
+        v.eps2 = c->eps * c->eps;
+      }
+    if (cudaMalloc(&c->sym_units, sizeof(nb::Unit) * M * P) != cudaSuccess)
       return fail(NBODY_ENOMEM, "diagonal-block units");
-    CK(cudaMemcpy(c->sym_units, u.data(), sizeof(nb::Unit) * M, cudaMemcpyHostToDevice));
-    c->sym_units_m = M;
+    CK(cudaMemcpy(c->sym_units, u.data(), sizeof(nb::Unit) * M * P, cudaMemcpyHostToDevice));
+    c->sym_units_m = M * P;
   }
   if (!c->sym_d && nd > 0) {
     // enough work items per launch for ~32 waves, within 1 GiB of buffers
@@ -205,12 +220,12 @@ static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
                              c->anchor, c->st, true));
     c->launches++;
   }
-  CK(nb::launch_force_units(c->mode, posm_in, c->fpos, c->anchor, c->sym_units, M,
+  CK(nb::launch_force_units(c->mode, posm_in, c->fpos, c->anchor, c->sym_units, (int64_t)M * P,
                             ff ? nb::sym_r_ff() : nb::sym_r(), c->part, 0, c->st));
   c->launches++;
-  S = 1;
+  S = P;
   if (nd == 0) return NBODY_OK;
-  nb::d4 *part = (nb::d4 *)c->part;
+  nb::d4 *part = (nb::d4 *)c->part + (int64_t)(P - 1) * c->n;  // rows in slice P, columns in P + 1
   nb::d4 *rows = (nb::d4 *)c->sym_buf, *cols = rows + (int64_t)c->sym_d * c->n;
   for (int d0 = 1; d0 <= nd; d0 += c->sym_d) {
     const int D = std::min(c->sym_d, nd - d0 + 1);
@@ -223,7 +238,7 @@ static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
     CK(nb::launch_sym_combine(rows, cols, D, c->n, part + c->n, part + 2 * c->n, d0 == 1, c->st));
     c->launches += 2;
   }
-  S = 3;
+  S = P + 2;
   return NBODY_OK;
 }
 

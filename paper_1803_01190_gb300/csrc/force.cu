@@ -319,6 +319,16 @@ __global__ void __launch_bounds__(BT) k_force_f64(const d4 *__restrict__ posm, W
           for (int r = 0; r < R; r++)
             body_f64<false>(pj, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pt[r], false);
         }
+      } else if (cnt == T) {  // a full tile that holds some of this block's own i
+  #pragma unroll 2
+        for (int k = 0; k < T; k++) {
+          const d4 pj = tile[k];
+          const int64_t j = jt + k;
+  #pragma unroll
+          for (int r = 0; r < R; r++)
+            body_f64<true>(pj, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pt[r],
+                           j == u.i0 + r * BT + tid);
+        }
       } else {
         for (int k = 0; k < cnt; k++) {
           const d4 pj = tile[k];
