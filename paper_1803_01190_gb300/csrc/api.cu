@@ -179,7 +179,9 @@ static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
                                                                       ff ? nb::sym_r_ff() : nb::sym_r(),
                                                                       nb::force_tile(c->mode), 1});
   const int64_t slots_1 = (int64_t)c->num_sms * std::max(1, per_sm_1);
-  const int P = (int)std::max<int64_t>(1, std::min<int64_t>(ff ? 2 : 4, (2 * slots_1 + M - 1) / M));
+  const int64_t want = (2 * slots_1 + M - 1) / M;
+  int P = 1;  // a power of two dividing the block size
+  while (P < want && P < (ff ? 2 : 4)) P *= 2;
   int rc = ensure_part(c, P + 2);
   if (rc) return rc;
   if (c->sym_units_m != M * P) {
@@ -194,7 +196,8 @@ static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
         v.i0 = (int64_t)I * B;
         v.ni = (int32_t)std::min<int64_t>(B, c->n - v.i0);
         v.j0 = v.i0 + q * len;
-        v.nj = (int32_t)std::max<int64_t>(0, std::min<int64_t>(len, c->n - v.j0));
+        const int64_t part_len = q == P - 1 ? B - q * len : len;  // the last part takes any remainder
+        v.nj = (int32_t)std::max<int64_t>(0, std::min<int64_t>(part_len, c->n - v.j0));
         v.out = (int64_t)q * c->n + v.i0;
         v.anchor = ff ? I : 0;  // F64E: block I is float-float tile I
         v.eps2 = c->eps * c->eps;

@@ -178,6 +178,21 @@ def test_f64e_symmetric_against_one_sided_and_kdk(nb):
     assert np.abs(v - ov).max() <= 1e-11 * np.abs(ov).max()
 
 
+@pytest.mark.parametrize("mode", ["fp64", "f64e"])
+def test_symmetric_many_blocks_sampled(nb, mode):
+    """N = 2^18 + 77: 513 FP64 blocks (1025 F64E tiles), several launch groups
+    of block diagonals, diagonal blocks split into parts, ragged tail; sampled
+    particles from every block against the oracle."""
+    n = 2 ** 18 + 77
+    pos, _, _ = nbody_ics.uniform_sphere(n, 51)
+    mass = nbody_ics.lognormal_masses(n, 52)
+    with nb.Simulation(n, mode, eps=1e-3) as sim:
+        assert sim.get_symmetric() == (-1, True)
+        acc, pot = sim.accel(pos, mass)
+    rows = np.unique(np.concatenate([np.arange(0, n, 509), np.arange(n - 600, n)]))
+    _check_fp64(acc, pot, pos, mass, 1e-3, rows=rows)
+
+
 def test_fp64_symmetric_auto_and_off(nb):
     w = nbody_ics.workload("disk_halo", n=40000)
     with nb.Simulation(40000, "fp64", eps=w["eps"]) as sim:
