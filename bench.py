@@ -429,7 +429,8 @@ def run_gpu(args):
                  "speedup_vs_fp64": (world * inter / (msfe * 1e-3) / 1e9) / value,
                  "force_ms_per_launch": f64e["force_ms"],
                  "note": "binary64-class float-float arithmetic on the FP32 pipes (about 48 bits)",
-                 "roofline": {"bound": "alu", "kernel": "k_force_f64e",
+                 "roofline": {"bound": "alu",
+                              "kernel": "k_force_f64e_sym" if f64e["sim"].get_symmetric()[1] else "k_force_f64e",
                               "achieved": inter * FLOP_PER_INTERACTION / (f64e["force_ms"] * 1e-3) / 1e12,
                               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                               "frac": inter * FLOP_PER_INTERACTION / (f64e["force_ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
