@@ -15,7 +15,7 @@
 // the epilogue kernels in update.cu sum the segments in a fixed order, apply
 // G and the update of the integrator.
 //
-// Three arithmetics:
+// Four arithmetics:
 //   f64   binary64 pair arithmetic.  GB300 issues binary64 at about 1/72 of the
 //         binary32 rate, so the kernel is bound by the FP64 pipe and its cost
 //         is its count of FP64 instructions per pair: 9 (3 DADD for d,
@@ -28,16 +28,18 @@
 //         evaluates each pair once for both particles (k_force_f64_sym:
 //         14 FP64 instructions per pair, 7 per interaction).
 //   mixed binary32 pair arithmetic (packed: two j per instruction, SFU
-//         reciprocal square root) on coordinates
-//         re-centred on an anchor (the per-coordinate median) per j-tile, with the i coordinates held as float-float pairs so that the
-//         per-tile shift costs three binary32 operations per coordinate and no
-//         FP64 instruction; per-tile binary32 partial sums are folded into
-//         float-float (compensated, TwoSum) accumulators, returned as binary64.
+//         reciprocal square root) on coordinates re-centred on an anchor (the
+//         per-coordinate median) per j-tile, with the i coordinates held as
+//         float-float pairs so that the per-tile shift costs three binary32
+//         operations per coordinate and no FP64 instruction; per-tile binary32
+//         partial sums are folded into float-float (compensated, TwoSum)
+//         accumulators, returned as binary64.
 //   f64e  binary64-class accuracy on the binary32 pipes: float-float (about 48
 //         significant bits) pair arithmetic on coordinates re-centred per
 //         j-tile, float-float tile partials folded into binary64 per tile.
 //         About 160 binary32 instructions per pair, but on pipes 64 times
-//         faster than GB300's FP64 pipe.
+//         faster than GB300's FP64 pipe.  From 64 blocks of 256 particles it
+//         evaluates each pair once for both particles (k_force_f64e_sym).
 //   f32   binary32 throughout (packed pairs, SFU reciprocal square root) with
 //         plain binary32 accumulation: the paper's SP.  The two halves of a
 //         thread's packed accumulators (even and odd j) are added at the end.
