@@ -194,6 +194,10 @@ int nbody_get_launch(nbody_ctx *ctx, int *ipt, int *jsplit, int *threads, int *t
  * blocks of 512 (FP64) or 256 (F64E).  mode = -1 (default): automatic, used
  * when n spans at least 64 blocks; 0: never; 1: whenever n spans at least 2
  * blocks.  The launch shape of nbody_set_launch does not apply to this path.
+ * Memory: the first force evaluation on this path allocates the context's
+ * per-diagonal row and column buffers (2 x D x n x 32 bytes, at most 1 GiB;
+ * D = 8 at n = 2^20 in FP64) and P + 2 slices of partial sums (P <= 4);
+ * mode 0 avoids both.
  * Errors: EINVAL (NULL context, mode outside -1..1, mode 1 in MIXED or FP32).
  */
 int nbody_set_symmetric(nbody_ctx *ctx, int mode);
