@@ -473,6 +473,8 @@ def profile_force(args):
     import paper_1803_01190_gb300 as nb
     w = nbody_ics.workload("disk_halo", n=args.n)
     with nb.Simulation(args.n, mode=args.profile_force, eps=EPS) as sim:
+        if args.symmetric != -1:
+            sim.set_symmetric(args.symmetric)
         sim.accel(w["pos"], w["mass"])
         torch.cuda.synchronize()
     print(json.dumps({"profile_force": args.profile_force, "n": args.n}))
@@ -606,6 +608,8 @@ def main():
     ap.add_argument("--evolution-out", default=None, help="npz file for the maps and curves")
     ap.add_argument("--drift-dt", type=float, default=DT)
     ap.add_argument("--drift-every", type=int, default=100)
+    ap.add_argument("--symmetric", type=int, choices=[-1, 0, 1], default=-1,
+                    help="--profile-force: each-pair-once path -1 automatic, 0 off, 1 on")
     ap.add_argument("--profile-force", choices=["fp64", "f64e", "mixed", "fp32"], default=None,
                     help="run one force evaluation of the workload in this mode and exit")
     args = ap.parse_args()
