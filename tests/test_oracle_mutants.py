@@ -24,6 +24,8 @@ MUTANTS = {
     "transposed_dy": ("double dy = yi - pos[3 * j + 1];", "double dy = pos[3 * j + 1] - yi;"),
     "index_z_from_y": ("double dz = zi - pos[3 * j + 2];", "double dz = zi - pos[3 * j + 1];"),
     "pot_sign": ("nsum_add(&p, -gm / soft);", "nsum_add(&p, gm / soft);"),
+    "smag_d2_not_distance": ("nsum_add(&s, gm * sqrt(d2) / w);", "nsum_add(&s, gm * d2 / w);"),
+    "smag_soft_not_distance": ("nsum_add(&s, gm * sqrt(d2) / w);", "nsum_add(&s, gm * soft / w);"),
     "kdk_drift_first_order": ("pos[k] = pos[k] + (dt / 2) * (vt[k] + vel[k]);", "pos[k] = pos[k] + dt * vel[k];"),
     "kdk_corrector_no_average": ("vel[k] = (vel[k] + vt[k]) / 2 + (dt / 2) * acc[k];", "vel[k] = vt[k] + (dt / 2) * acc[k];"),
     "kdk_predictor_half": ("vt[k] = vel[k] + dt * acc[k];", "vt[k] = vel[k] + (dt / 2) * acc[k];"),

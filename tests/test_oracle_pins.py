@@ -38,12 +38,14 @@ def test_point_mass_and_test_particles(oracle, eps):
     M, G = 2.5, 0.7
     pos = np.vstack([[0.0, 0.0, 0.0], r[:, None] * d])   # d_ij is then exactly r d
     mass = np.concatenate([[M], np.zeros(k)])
-    acc, pot, _ = oracle.accel(pos, mass, eps, G)
+    acc, pot, smag = oracle.accel(pos, mass, eps, G)
     w = (pos[1:] ** 2).sum(1) + eps * eps
     want = -G * M * pos[1:] / w[:, None] ** 1.5
     np.testing.assert_allclose(acc[1:], want, rtol=4e-15, atol=0)
     np.testing.assert_allclose(pot[1:], -G * M / np.sqrt(w), rtol=4e-15, atol=0)
-    assert np.all(acc[0] == 0.0) and pot[0] == 0.0
+    # the magnitude sum of a single term is that term's magnitude, G M r / (r^2 + eps^2)^{3/2}
+    np.testing.assert_allclose(smag[1:], G * M * r / w ** 1.5, rtol=4e-15, atol=0)
+    assert np.all(acc[0] == 0.0) and pot[0] == 0.0 and smag[0] == 0.0
 
 
 @pytest.mark.parametrize("eps", [0.0, 0.05])
@@ -81,21 +83,26 @@ def _decimal_brute(pos, mass, eps, G):
     Gd = D(float(G))
     acc = np.zeros((n, 3))
     pot = np.zeros(n)
+    mag = np.zeros(n)
     for i in range(n):
         a = [D(0)] * 3
         p = D(0)
+        sm = D(0)
         for j in range(n):
             if j == i:
                 continue
             d = [P[i][c] - P[j][c] for c in range(3)]
-            s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + e2
+            r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2]
+            s2 = r2 + e2
             s = s2.sqrt()
             for c in range(3):
                 a[c] -= Gd * Mm[j] * d[c] / (s2 * s)
             p -= Gd * Mm[j] / s
+            sm += Gd * Mm[j] * r2.sqrt() / (s2 * s)   # |term|: the length of the pair's force
         acc[i] = [float(x) for x in a]
         pot[i] = float(p)
-    return acc, pot
+        mag[i] = float(sm)
+    return acc, pot, mag
 
 
 @pytest.mark.parametrize("n,eps", [(2, 0.0), (7, 0.01), (33, 0.3), (64, 1e-3)])
@@ -105,8 +112,11 @@ def test_brute_force_40_digits(oracle, n, eps):
     pos = nbody_ics.plummer(n, 100 + n)[0]
     mass = nbody_ics.lognormal_masses(n, 200 + n)
     acc, pot, smag = oracle.accel(pos, mass, eps, 1.1)
-    ea, ep = _decimal_brute(pos, mass, eps, 1.1)
-    assert np.all(np.abs(acc - ea) <= 4 * U * smag[:, None] + 1e-300)
+    ea, ep, es = _decimal_brute(pos, mass, eps, 1.1)
+    # smag is pinned first (terms of one sign: a few roundings each), because it
+    # then sets the scale of the acceleration bound below
+    assert np.all(np.abs(smag - es) <= 8 * U * es)
+    assert np.all(np.abs(acc - ea) <= 4 * U * es[:, None] + 1e-300)
     assert np.all(np.abs(pot - ep) <= 4 * U * np.abs(ep))
 
 
