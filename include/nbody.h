@@ -332,11 +332,14 @@ int64_t nbody_batch_launch_count(const nbody_batch *b);
  * NBODY_STATIC_MAX_N, and a larger n returns NBODY_EINVAL before any launch.
  * All calls share that array (nothing in it needs clearing between calls), so
  * calls whose work overlaps on the GPU (several streams or host threads) race
- * and give wrong results: order them on one stream.  The first call on each
- * device looks up the array's device address with that device current; make
- * that first call before any stream capture begins.
- * Errors: EINVAL (n < 1, n > NBODY_STATIC_MAX_N, NULL pos/mass/acc, eps < 0 or
- * non-finite, G non-finite), ECUDA.
+ * and give wrong results: order them on one stream.  The array's device
+ * address is looked up once per CUDA context with that context current (the
+ * first call in a device's primary context, again after cudaDeviceReset, and
+ * in any other context the caller makes current); make that first call before
+ * any stream capture begins.  Inputs are not scanned for non-finite values
+ * (as in nbody_accel): a NaN input gives NaN outputs.
+ * Errors (detail in nbody_last_error): EINVAL (n < 1, n > NBODY_STATIC_MAX_N,
+ * NULL pos/mass/acc, eps < 0 or non-finite, G non-finite), ECUDA.
  */
 #define NBODY_STATIC_MAX_N 32768
 #define NBODY_STATIC_SCRATCH_BYTES (16 * 1024 * 1024)

@@ -69,6 +69,8 @@ static int fail(int code, const char *what, cudaError_t ce = cudaSuccess) {
   return code;
 }
 
+int nb::record_error(int code, const char *what, cudaError_t ce) { return fail(code, what, ce); }
+
 #define CK(call)                                                         \
   do {                                                                   \
     cudaError_t e_ = (call);                                             \

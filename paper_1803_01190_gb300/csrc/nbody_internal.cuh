@@ -142,6 +142,10 @@ cudaError_t launch_diag(int mode, const void *posm, const void *vel, const void 
                         double *blocks, int nblocks, double *out9, cudaStream_t st);
 int diag_blocks(int64_t n);
 
+// Records the detail that nbody_last_error() returns on this thread and
+// returns `code` (api.cu); every entry point reports its failures through it.
+int record_error(int code, const char *what, cudaError_t ce = cudaSuccess);
+
 inline size_t real_bytes(int mode) { return mode == NBODY_FP32 ? sizeof(float) : sizeof(double); }
 
 }  // namespace nb

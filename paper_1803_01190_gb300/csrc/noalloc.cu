@@ -18,9 +18,13 @@
 //     calls whose work overlaps on the GPU (different streams, or different
 //     host threads) race on it and give wrong results.  Order them on one
 //     stream or serialise them.
-//   - the first call on a device looks up the array's device address with that
-//     device current (a one-time set-up per device); make that first call
-//     before any stream capture begins.
+//   - the array's device address is looked up once per CUDA context, with
+//     that context current: on the first call of a device's primary context,
+//     again after cudaDeviceReset (which makes a new one), and for any other
+//     context the caller makes current.  Make that first call before any
+//     stream capture begins.
+//   - inputs are not scanned for non-finite values (as in nbody_accel); a NaN
+//     input gives NaN outputs.
 // The paper has no counterpart of this entry point.
 #include <cuda_runtime.h>
 
@@ -39,33 +43,81 @@ static_assert(kScratchBytes >= (size_t)kMaxN * sizeof(nb::d4) * 3, "scratch too 
 // address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
+// Driver entry points for the identity of the current context, looked up once
+// through the runtime (the library links only the CUDA runtime).
+using CtxGetCurrent = int (*)(void **);                  // cuCtxGetCurrent
+using CtxGetId = int (*)(void *, unsigned long long *);  // cuCtxGetId
+
+// One cached address per context, keyed by the context's unique id (ids are
+// never reused within a process, unlike context handles).
+constexpr int kCache = 64;
+struct Entry {
+  unsigned long long id;
+  void *addr;
+  int sms;
+};
 std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
-int g_sms[kMaxDevices] = {};
+Entry g_cache[kCache] = {};
+int g_used = 0, g_next = 0;
+CtxGetCurrent g_get_current = nullptr;
+CtxGetId g_get_id = nullptr;
 
-// Errors are reported by code only (the codes of include/nbody.h).
-int fail(int code, const char *, cudaError_t = cudaSuccess) { return code; }
+int fail(int code, const char *what, cudaError_t ce = cudaSuccess) {
+  return nb::record_error(code, what, ce);
+}
 
-// Device address of g_scratch on the current device, looked up once per device.
-int scratch_for_current_device(void **addr, int *sms) {
-  int dev = 0;
-  cudaError_t ce = cudaGetDevice(&dev);
-  if (ce != cudaSuccess) return fail(NBODY_ECUDA, "cudaGetDevice", ce);
-  if (dev < 0 || dev >= kMaxDevices) return fail(NBODY_EINVAL, "device ordinal out of range");
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    ce = cudaGetSymbolAddress(&p, g_scratch);
-    if (ce != cudaSuccess || !p) return fail(NBODY_ECUDA, "cudaGetSymbolAddress(scratch)", ce);
-    int s = 0;
-    ce = cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
-    if (ce != cudaSuccess) return fail(NBODY_ECUDA, "cudaDeviceGetAttribute", ce);
-    g_addr[dev] = p;
-    g_sms[dev] = s;
+int current_context_id(unsigned long long *id) {
+  if (!g_get_current || !g_get_id) {
+    void *a = nullptr, *b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    cudaError_t ce = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000,
+                                                      cudaEnableDefault, &qa);
+    if (ce == cudaSuccess)
+      ce = cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb);
+    if (ce != cudaSuccess || qa != cudaDriverEntryPointSuccess ||
+        qb != cudaDriverEntryPointSuccess || !a || !b)
+      return fail(NBODY_ECUDA, "driver entry points cuCtxGetCurrent/cuCtxGetId", ce);
+    g_get_current = (CtxGetCurrent)a;
+    g_get_id = (CtxGetId)b;
   }
-  *addr = g_addr[dev];
-  *sms = g_sms[dev];
+  void *ctx = nullptr;
+  if (g_get_current(&ctx) != 0) return fail(NBODY_ECUDA, "cuCtxGetCurrent");
+  if (!ctx) {
+    // nothing current yet: bind the current device's primary context, as the
+    // runtime does before any launch
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaSetDevice(dev);
+    if (ce != cudaSuccess) return fail(NBODY_ECUDA, "primary context", ce);
+    if (g_get_current(&ctx) != 0 || !ctx) return fail(NBODY_ECUDA, "no current CUDA context");
+  }
+  if (g_get_id(ctx, id) != 0) return fail(NBODY_ECUDA, "cuCtxGetId");
+  return NBODY_OK;
+}
+
+// Device address of g_scratch in the current context and the device's SM count.
+int scratch_for_current_context(void **addr, int *sms) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  unsigned long long id = 0;
+  int rc = current_context_id(&id);
+  if (rc) return rc;
+  for (int k = 0; k < g_used; k++)
+    if (g_cache[k].id == id) {
+      *addr = g_cache[k].addr;
+      *sms = g_cache[k].sms;
+      return NBODY_OK;
+    }
+  void *p = nullptr;
+  cudaError_t ce = cudaGetSymbolAddress(&p, g_scratch);
+  if (ce != cudaSuccess || !p) return fail(NBODY_ECUDA, "cudaGetSymbolAddress(scratch)", ce);
+  int dev = 0, s = 0;
+  ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+  if (ce != cudaSuccess) return fail(NBODY_ECUDA, "SM count", ce);
+  Entry &e = g_cache[g_used < kCache ? g_used++ : (g_next++ % kCache)];
+  e = Entry{id, p, s};
+  *addr = p;
+  *sms = s;
   return NBODY_OK;
 }
 
@@ -80,7 +132,7 @@ extern "C" int nbody_accel_f64_static(int64_t n, const double *pos, const double
     return fail(NBODY_EINVAL, "eps must be finite and >= 0, G finite");
   void *base = nullptr;
   int sms = 0;
-  int rc = scratch_for_current_device(&base, &sms);
+  int rc = scratch_for_current_context(&base, &sms);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)cuda_stream;
 
@@ -91,8 +143,8 @@ extern "C" int nbody_accel_f64_static(int64_t n, const double *pos, const double
   const int64_t slots = (int64_t)(kScratchBytes / sizeof(nb::d4)) / n - 2;
 
   nb::Shape sh;
-  sh.bt = 128;
-  sh.t = 128;
+  sh.bt = nb::force_block_threads(NBODY_FP64);
+  sh.t = nb::force_tile(NBODY_FP64);
   sh.r = 4;
   while (sh.r > 1 && (int64_t)sh.bt * sh.r * sms > n) sh.r >>= 1;
   const int64_t bx = (n + (int64_t)sh.bt * sh.r - 1) / ((int64_t)sh.bt * sh.r);
