@@ -33,17 +33,20 @@ UNIT = "Ginteractions/s"
 FLOP_PER_INTERACTION = 20
 N_FULL = 2 ** 20
 EPS, DT = 0.02, 5e-4
-SMS, FP64_PER_CLK, FP32_PER_CLK, SM_MAX_GHZ = 152, 2, 128, 2.07
-# derived ALU peaks (flop/s): SMs x lanes-per-clock x 2 (FMA) x max SM clock
-FP64_PEAK_TFLOPS = SMS * FP64_PER_CLK * 2 * SM_MAX_GHZ / 1e3
-# FP64-pipe instruction rate (instructions/s) and the FP64 instructions the two
-# binary64 force paths issue per interaction: 9 one-sided (3 DADD, 3 DFMA for
+# Work each force kernel issues on the pipe that bounds it, per interaction
+# (counted from the kernels' source, confirmed by ncu instruction counts):
+# FP64 pipe instructions of the binary64 paths: 9 one-sided (3 DADD, 3 DFMA for
 # |d|^2 + eps^2, 3 DFMA for the acceleration sums; the potential sum is an
 # integer add); 14 per pair evaluated once for both particles, i.e. 7 per
-# interaction
-FP64_PIPE_GINSTR = SMS * FP64_PER_CLK * SM_MAX_GHZ
+# interaction.
 FP64_INSTR_PER_INTERACTION = {False: 9, True: 7}
-FP32_PEAK_TFLOPS = SMS * FP32_PER_CLK * 2 * SM_MAX_GHZ / 1e3
+# FP32 FMA-pipe lane operations: mixed 13 (3 differences, 3 FMAs for
+# |d|^2 + eps^2, m y, y^2, m y^3, 3 FMAs and 1 add into the sums; two j per
+# packed instruction); F64E float-float 162 one-sided, 112 per interaction
+# when each pair is evaluated once (ncu: 111.8 packed FMA-pipe instructions
+# per pair evaluation).
+MIXED_LANEOPS_PER_INTERACTION = 13
+F64E_LANEOPS_PER_INTERACTION = {False: 162, True: 112}
 
 
 # DRAM traffic of one FP64 force launch at N = 2^20 (dram__bytes_read.sum +
@@ -318,6 +321,8 @@ def run_gpu(args):
     flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
     clocks = ClockSampler(local)
     inter = float(n) * n
+    # pipe issue rates of this GPU, measured in this run: the roofline denominators
+    pipes = nb.measure_pipes()
 
     fp64 = time_mode(nb, torch, w, "fp64", args, flush, clocks=clocks)
     mixed = time_mode(nb, torch, w, "mixed", args, flush)
@@ -360,6 +365,9 @@ def run_gpu(args):
     afe, _ = f64e["sim"].get_accel()
     aofe, _, smag_fe = oracle.accel(pfe, w["mass"], EPS, 1.0, rows=rows, threads=cores)
     cpu_value = len(rows) * n / cpu_s / 1e9
+    t0 = time.perf_counter()
+    oracle.plain_accel(p64, w["mass"], EPS, 1.0, rows=rows, threads=cores)
+    plain_s = time.perf_counter() - t0
 
     def errs(a, ao):
         e = np.linalg.norm(a[rows] - ao, axis=1) / np.linalg.norm(ao, axis=1)
@@ -388,30 +396,7 @@ def run_gpu(args):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "launch": {**fp64["sim"].get_launch(), "each_pair_once": sym}},
         "p50_step_ms": float(np.percentile(per, 50)), "p99_step_ms": float(np.percentile(per, 99)),
-        "roofline": {"bound": "alu", "kernel": "k_force_f64_sym" if sym else "k_force_f64",
-                     "achieved": achieved_tf,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": traffic_f64(n, sym),
-                     "traffic_note": ("DRAM bytes per force evaluation from one full-size ncu capture: "
-                                      "mostly the per-diagonal row/column slices of the each-pair-once "
-                                      "schedule, O(N^2/512), far above the O(N) algorithmic bytes but "
-                                      "~0.2% of HBM bandwidth over the evaluation" if sym else
-                                      "DRAM bytes per force evaluation from one full-size ncu capture; the "
-                                      "O(N) algorithmic bytes (32 B in + partial sums out per particle) "
-                                      "mostly stay in the 129 MB L2"),
-                     "flop_convention": f"{FLOP_PER_INTERACTION} flop/interaction x N^2 per force evaluation"
-                                        + ("; each pair is evaluated once for both particles, so the "
-                                           "convention can exceed the FP64 peak: fp64_pipe.frac is the "
-                                           "utilisation of the bounding pipe" if sym else ""),
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                     "fp64_pipe": {"instr_per_interaction": FP64_INSTR_PER_INTERACTION[sym],
-                                   "achieved_ginstr_s": inter * FP64_INSTR_PER_INTERACTION[sym]
-                                   / (fms * 1e-3) / 1e9,
-                                   "peak_ginstr_s": FP64_PIPE_GINSTR,
-                                   "frac": inter * FP64_INSTR_PER_INTERACTION[sym] / (fms * 1e-3) / 1e9
-                                   / FP64_PIPE_GINSTR},
-                     "force_ms_per_launch": fms, "force_ms_note": "one force evaluation (all its launches)",
-                     "force_share_of_step": fms / ms64},
+        "roofline": roofline_fp64(n, sym, fms, ms64, pipes),
         "gpu_launches": fp64["launches"] * world,
         "clocks": fp64["clocks"],
         "e2e": {"value": world * inter / e2e64["sec"] / 1e9, "unit": UNIT,
@@ -419,7 +404,12 @@ def run_gpu(args):
                 "call": "nbody_accel (host pinned buffers), FP64", "steps": args.e2e_steps},
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{len(rows)} sampled i-particles x all {n} j of the FP64 "
-                                   f"state after the timed steps ({cpu_s:.1f} s)"},
+                                   f"state after the timed steps ({cpu_s:.1f} s)",
+                         "plain_loop": {"value": len(rows) * n / plain_s / 1e9, "unit": UNIT,
+                                        "cores": cores, "kind": "plain binary64 OpenMP simd loop, "
+                                        "no compensation, -O3 (the CPU throughput figure)",
+                                        "sample": f"the same {len(rows)} i-particles ({plain_s:.1f} s)"}},
+        "pipes": pipes,
         "force_error_vs_oracle": {"fp64": {**errs(a64, ao64), "gate_1e-12_pass": bool(gate.all())},
                                   "f64e": {**errs(afe, aofe), "gate_1e-12_pass_fraction": float(np.mean(
                                       np.linalg.norm(afe[rows] - aofe, axis=1) <= 1e-12 * np.linalg.norm(aofe, axis=1)
@@ -429,23 +419,19 @@ def run_gpu(args):
                  "speedup_vs_fp64": (world * inter / (msfe * 1e-3) / 1e9) / value,
                  "force_ms_per_launch": f64e["force_ms"],
                  "note": "binary64-class float-float arithmetic on the FP32 pipes (about 48 bits)",
-                 "roofline": {"bound": "alu",
-                              "kernel": "k_force_f64e_sym" if f64e["sim"].get_symmetric()[1] else "k_force_f64e",
-                              "achieved": inter * FLOP_PER_INTERACTION / (f64e["force_ms"] * 1e-3) / 1e12,
-                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                              "frac": inter * FLOP_PER_INTERACTION / (f64e["force_ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
-                              "peak_source": "the FP64 peak it replaces (derived, 1.259 TFLOP/s)"},
+                 "roofline": roofline_fp32_pipe(
+                     "k_force_f64e_sym" if f64e["sim"].get_symmetric()[1] else "k_force_f64e",
+                     F64E_LANEOPS_PER_INTERACTION[f64e["sim"].get_symmetric()[1]], n, f64e["force_ms"],
+                     pipes),
                  "gpu_launches": f64e["launches"] * world, "launch": f64e["sim"].get_launch()},
         "mixed": {"value": value_mx, "unit": UNIT, "ms_per_step": msmx,
                   "speedup_vs_fp64": value_mx / value,
                   "p50_step_ms": float(np.percentile(mixed["per_step"], 50)),
                   "p99_step_ms": float(np.percentile(mixed["per_step"], 99)),
                   "force_ms_per_launch": mixed["force_ms"],
-                  "roofline": {"bound": "alu", "kernel": "k_force_mixed",
-                               "achieved": inter * FLOP_PER_INTERACTION / (mixed["force_ms"] * 1e-3) / 1e12,
-                               "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                               "frac": inter * FLOP_PER_INTERACTION / (mixed["force_ms"] * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
-                               "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"},
+                  "roofline": roofline_fp32_pipe("k_force_mixed", MIXED_LANEOPS_PER_INTERACTION, n,
+                                                 mixed["force_ms"], pipes),
+                  "order": mixed["sim"].get_order(),
                   "e2e": {"value": world * inter / e2emx["sec"] / 1e9, "unit": UNIT},
                   "gpu_launches": mixed["launches"] * world,
                   "launch": mixed["sim"].get_launch()},
@@ -465,6 +451,60 @@ def run_gpu(args):
         torch.distributed.barrier()
 
 
+def roofline_fp64(n, sym, force_ms, step_ms, pipes):
+    """The binary64 force path is bound by the FP64 pipe: achieved = its FP64
+    instructions per interaction x N^2 / the force evaluation's CUDA-event
+    time; peak = the DFMA issue rate measured in the same run."""
+    inter = float(n) * n
+    ipi = FP64_INSTR_PER_INTERACTION[sym]
+    achieved = inter * ipi / (force_ms * 1e-3) / 1e9
+    conv = inter * FLOP_PER_INTERACTION / (force_ms * 1e-3) / 1e12
+    return {"bound": "alu", "pipe": "fp64", "kernel": "k_force_f64_sym" if sym else "k_force_f64",
+            "achieved": achieved, "peak": pipes["dfma_ginstr_s"], "unit": "G FP64-pipe instr/s",
+            "frac": achieved / pipes["dfma_ginstr_s"],
+            "peak_source": (f"measured in this run: nbody_measure_pipes DFMA issue rate "
+                            f"({pipes['dfma_per_clk_sm']:.3f}/clk/SM x {pipes['sms']:.0f} SMs at "
+                            f"{pipes['sm_mhz']:.0f} MHz)"),
+            "instr_per_interaction": ipi,
+            "traffic": traffic_f64(n, sym),
+            "traffic_note": ("DRAM bytes per force evaluation from one full-size ncu capture: mostly the "
+                             "per-diagonal row/column slices of the each-pair-once schedule, O(N^2/512), far "
+                             "above the O(N) algorithmic bytes but ~0.2% of HBM bandwidth over the evaluation"
+                             if sym else
+                             "DRAM bytes per force evaluation from one full-size ncu capture; the O(N) "
+                             "algorithmic bytes (32 B in + partial sums out per particle) mostly stay in L2"),
+            "convention_20flop": {"achieved": conv, "peak": 2 * pipes["dfma_ginstr_s"] / 1e3,
+                                  "unit": "TFLOP/s", "frac": conv / (2 * pipes["dfma_ginstr_s"] / 1e3),
+                                  "note": "20 flop/interaction x N^2 against 2 flop per measured DFMA; "
+                                          + ("each pair is evaluated once for both particles, so this "
+                                             "can exceed 1" if sym else "")},
+            "force_ms_per_launch": force_ms, "force_ms_note": "one force evaluation (all its launches)",
+            "force_share_of_step": force_ms / step_ms}
+
+
+def roofline_fp32_pipe(kernel, laneops, n, force_ms, pipes):
+    """Kernels on the binary32 FMA pipes (mixed, F64E): achieved = FMA-pipe lane
+    operations per interaction x N^2 / force time; peak = the packed FFMA2
+    lane-operation rate measured in the same run."""
+    inter = float(n) * n
+    achieved = inter * laneops / (force_ms * 1e-3) / 1e9
+    conv = inter * FLOP_PER_INTERACTION / (force_ms * 1e-3) / 1e12
+    return {"bound": "alu", "pipe": "fp32 fma", "kernel": kernel, "achieved": achieved,
+            "peak": pipes["ffma2_glane_s"], "unit": "G FMA-pipe lane-ops/s",
+            "frac": achieved / pipes["ffma2_glane_s"], "laneops_per_interaction": laneops,
+            "peak_source": (f"measured in this run: nbody_measure_pipes packed FFMA2 lane-op rate "
+                            f"({pipes['ffma2_lane_per_clk_sm']:.1f}/clk/SM at {pipes['sm_mhz']:.0f} MHz)"),
+            "convention_20flop_tflops": conv, "force_ms_per_launch": force_ms}
+
+
+def run_peaks(args):
+    """The measured pipe rates alone (nbody_measure_pipes), as one JSON line."""
+    import torch
+    import paper_1803_01190_gb300 as nb
+    torch.cuda.set_device(0)
+    print(json.dumps({"pipes": nb.measure_pipes(), "gpu": torch.cuda.get_device_name(0)}), flush=True)
+
+
 def profile_force(args):
     """One force evaluation (Eq. 1-2) of the benchmark workload in one mode and
     nothing else: the command the ncu captures of a single force launch run."""
@@ -475,6 +515,8 @@ def profile_force(args):
     with nb.Simulation(args.n, mode=args.profile_force, eps=EPS) as sim:
         if args.symmetric != -1:
             sim.set_symmetric(args.symmetric)
+        if args.order != "default":
+            sim.set_order(args.order)
         sim.accel(w["pos"], w["mass"])
         torch.cuda.synchronize()
     print(json.dumps({"profile_force": args.profile_force, "n": args.n}))
@@ -494,6 +536,9 @@ def run_drift(args):
            "steps": args.drift_steps, "every": args.drift_every, "workload": workload_desc(args.n),
            "force_evaluations": args.drift_steps * {"kdk": 1, "fr4": 3, "rk4": 4}[args.drift_scheme]}
     with nb.Simulation(args.n, mode=args.drift, eps=EPS) as sim:
+        if args.order != "default":
+            sim.set_order(args.order)
+        out["order"] = sim.get_order()
         sim.set_state(w["pos"], w["vel"], w["mass"])
         d0 = sim.diagnostics()
         curve = []
@@ -612,10 +657,15 @@ def main():
                     help="--profile-force: each-pair-once path -1 automatic, 0 off, 1 on")
     ap.add_argument("--profile-force", choices=["fp64", "f64e", "mixed", "fp32"], default=None,
                     help="run one force evaluation of the workload in this mode and exit")
+    ap.add_argument("--order", choices=["default", "input", "spatial"], default="default",
+                    help="--profile-force / --drift: particle order of the force sum")
+    ap.add_argument("--peaks", action="store_true", help="print the measured pipe rates and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.drift:
+    if args.peaks:
+        run_peaks(args)
+    elif args.drift:
         run_drift(args)
     elif args.evolution:
         run_evolution(args)

@@ -204,6 +204,29 @@ int nbody_set_symmetric(nbody_ctx *ctx, int mode);
 /* The setting (-1, 0, 1) and whether the next force evaluation uses the path. */
 int nbody_get_symmetric(const nbody_ctx *ctx, int *mode, int *active);
 
+/*
+ * Particle order of the force sum (a project addition; the paper sums in input
+ * order).  NBODY_ORDER_SPATIAL sorts the particles along a Morton (Z-order)
+ * curve of their positions before each force evaluation (bounding box,
+ * 21-bit cells per coordinate, stable sort on the 63-bit keys) and runs the
+ * force kernels on the sorted copy; results come back in input order.  The
+ * order is a deterministic function of the positions, so results stay
+ * reproducible bit for bit.  It matters for NBODY_MIXED: the binary32
+ * coordinates relative to a j-tile's anchor keep their digits only when the
+ * tile is spatially compact (force error at eps = 1e-3 several times
+ * smaller), and it is the default there; NBODY_ORDER_INPUT elsewhere.
+ * FP64 and F64E accept either (the order changes only the summation order);
+ * NBODY_FP32 keeps input order (the paper's SP).
+ * Memory: the first force evaluation with the spatial order allocates about
+ * 96 + 32 S bytes per particle (keys, permutation, sorted copies of the
+ * positions and of the S partial-sum slices).
+ * Errors: EINVAL (NULL context, unknown order, NBODY_ORDER_SPATIAL in FP32).
+ */
+#define NBODY_ORDER_INPUT   0
+#define NBODY_ORDER_SPATIAL 1
+int nbody_set_order(nbody_ctx *ctx, int order);
+int nbody_get_order(const nbody_ctx *ctx, int *order);
+
 /* Number of kernel launches this context has issued since creation. */
 int64_t nbody_launch_count(const nbody_ctx *ctx);
 
@@ -217,6 +240,24 @@ int64_t nbody_launch_count(const nbody_ctx *ctx);
  */
 int nbody_profile(nbody_ctx *ctx, int enable);
 int nbody_profile_read(nbody_ctx *ctx, double *force_ms, int64_t *force_launches);
+
+/*
+ * Measured issue rates of the pipes that bound the force kernels, on the
+ * current device (the denominators of their rooflines; the paper reports no
+ * such figures).  Each rate is timed with CUDA events over a kernel that runs
+ * one full wave of resident blocks issuing only independent chains of one
+ * instruction; the SM clock is read from the cycle counter of one block of
+ * the binary64 kernel.  Runs about 0.2 s on the legacy default stream and
+ * synchronises the device.  out[0..NBODY_PIPE_FIELDS-1] receives:
+ *   0 SM count            1 SM clock [MHz] during the run
+ *   2 DFMA  [G instr/s]   3 FFMA lane-ops [G/s]   4 FFMA2 (packed) lane-ops [G/s]
+ *   5 MUFU.RSQ [G/s]      6 DFMA per clock per SM  7 FFMA2 lane-ops per clock per SM
+ *   8 MUFU.RSQ per clock per SM
+ * Allocates 16 bytes of device memory for the duration of the call.
+ * Errors: EINVAL (out NULL or nout < NBODY_PIPE_FIELDS), ENOMEM, ECUDA.
+ */
+#define NBODY_PIPE_FIELDS 9
+int nbody_measure_pipes(double *out, int nout);
 
 /* ======================================================================
  * Batched execution of many independent simulations (serving).

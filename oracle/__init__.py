@@ -170,3 +170,34 @@ def rk4(*a, **k):
 
 def diag(*a, **k):
     return default().diag(*a, **k)
+
+
+_plain = None
+
+
+def plain_accel(pos, mass, eps, G=1.0, rows=None, threads=0):
+    """The plain (uncompensated, vectorised) binary64 CPU loop of cpu_plain.c:
+    the benchmark's CPU throughput figure, never a parity reference.
+    Returns (acc (k,3), pot (k,))."""
+    global _plain
+    if _plain is None:
+        lib = ctypes.CDLL(_build.build_plain())
+        lib.plain_accel.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_int64, _ip, _dp, _dp, ctypes.c_int]
+        lib.plain_accel.restype = ctypes.c_int
+        lib.plain_max_threads.restype = ctypes.c_int
+        _plain = lib
+    pos = _f64(pos, (-1, 3))
+    mass = _f64(mass, (-1,))
+    n = pos.shape[0]
+    if rows is None:
+        k, rp = n, None
+    else:
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        k, rp = rows.shape[0], rows.ctypes.data_as(_ip)
+    acc = np.empty((k, 3))
+    pot = np.empty(k)
+    if _plain.plain_accel(n, _d(pos), _d(mass), float(eps), float(G), k, rp, _d(acc), _d(pot),
+                          int(threads)) != 0:
+        raise ValueError("plain_accel: bad argument")
+    return acc, pot

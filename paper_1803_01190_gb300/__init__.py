@@ -25,7 +25,8 @@ from ._abi import (F64E, FP32, FP64, FR4, KDK, MIXED, RK4, NbodyError, check, li
 MODES = {"fp64": FP64, "mixed": MIXED, "fp32": FP32, "f64e": F64E}
 SCHEMES = {"kdk": KDK, "rk4": RK4, "fr4": FR4}
 
-__all__ = ["Simulation", "NbodyError", "MODES", "SCHEMES", "lib", "library_path", "build"]
+__all__ = ["Simulation", "NbodyError", "MODES", "SCHEMES", "lib", "library_path", "build",
+           "measure_pipes"]
 
 
 def build(force=False):
@@ -68,6 +69,17 @@ def _current_stream():
     if t is not None and t.cuda.is_available():
         return ctypes.c_void_p(t.cuda.current_stream().cuda_stream)
     return ctypes.c_void_p(0)
+
+
+PIPE_FIELDS = ("sms", "sm_mhz", "dfma_ginstr_s", "ffma_glane_s", "ffma2_glane_s", "rsqrt_g_s",
+               "dfma_per_clk_sm", "ffma2_lane_per_clk_sm", "rsqrt_per_clk_sm")
+
+
+def measure_pipes():
+    """Measured pipe issue rates of the current device (nbody_measure_pipes)."""
+    out = (ctypes.c_double * len(PIPE_FIELDS))()
+    check(lib.nbody_measure_pipes(out, len(PIPE_FIELDS)), "nbody_measure_pipes")
+    return dict(zip(PIPE_FIELDS, (float(x) for x in out)))
 
 
 class Simulation:
@@ -189,6 +201,17 @@ class Simulation:
         m, a = ctypes.c_int(), ctypes.c_int()
         check(lib.nbody_get_symmetric(self._h, ctypes.byref(m), ctypes.byref(a)), "nbody_get_symmetric")
         return m.value, bool(a.value)
+
+    def set_order(self, order):
+        """Particle order of the force sum: "input" or "spatial" (Morton curve;
+        the default in mixed mode)."""
+        code = {"input": 0, "spatial": 1}[order]
+        check(lib.nbody_set_order(self._h, code), "nbody_set_order")
+
+    def get_order(self):
+        o = ctypes.c_int()
+        check(lib.nbody_get_order(self._h, ctypes.byref(o)), "nbody_get_order")
+        return ("input", "spatial")[o.value]
 
     def get_launch(self):
         v = [ctypes.c_int() for _ in range(4)]

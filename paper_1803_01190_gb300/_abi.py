@@ -46,6 +46,8 @@ _SIGS = {
                               ctypes.POINTER(_i)]),
     "nbody_set_symmetric": (_i, [_vp, _i]),
     "nbody_get_symmetric": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "nbody_set_order": (_i, [_vp, _i]),
+    "nbody_get_order": (_i, [_vp, ctypes.POINTER(_i)]),
     "nbody_launch_count": (_i64, [_vp]),
     "nbody_profile": (_i, [_vp, _i]),
     "nbody_profile_read": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_i64)]),
@@ -70,6 +72,7 @@ _SIGS = {
     "nbody_batch_profile_read": (_i, [_vp, _i64, _vp, _vp, _vp, ctypes.POINTER(_i64)]),
     "nbody_batch_launch_count": (_i64, [_vp]),
     "nbody_accel_f64_static": (_i, [_i64, _vp, _vp, _d, _d, _vp, _vp, _vp]),
+    "nbody_measure_pipes": (_i, [_dp, _i]),
 }
 
 for _name, (_res, _args) in _SIGS.items():

@@ -53,6 +53,15 @@ struct nbody_ctx {
   int sym_units_m = 0;
   void *sym_buf = nullptr;
   int sym_d = 0;
+  // particle order of the force sum: 0 = input order, 1 = spatial (Morton)
+  // order; order scratch, sorted-to-input permutation, sorted positions and
+  // the sorted partial sums (alt_slices slices of n)
+  int order = 0;
+  void *ord_scratch = nullptr;
+  int32_t *perm = nullptr;
+  d4 *sposm = nullptr;
+  void *part_alt = nullptr;
+  int alt_slices = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;  // all created events
   size_t ev_used = 0;                                          // pairs recorded since last read
 };
@@ -133,16 +142,28 @@ static int64_t seg_len(const nbody_ctx *c, int &S) {
   return seg;
 }
 
-static int ensure_part(nbody_ctx *c, int S) {
-  if (S <= c->part_slices) return NBODY_OK;
-  if (c->part) cudaFree(c->part);
-  c->part = nullptr;
-  c->part_slices = 0;
-  if (cudaMalloc(&c->part, (size_t)S * c->n * part_r4(c)) != cudaSuccess)
+static int ensure_slices(nbody_ctx *c, void **buf, int *have, int S) {
+  if (S <= *have) return NBODY_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *have = 0;
+  if (cudaMalloc(buf, (size_t)S * c->n * part_r4(c)) != cudaSuccess)
     return fail(NBODY_ENOMEM, "j-segment partial buffer");
-  c->part_slices = S;
+  *have = S;
   return NBODY_OK;
 }
+
+// S slices of partial sums in c->part and, with the spatial order, as many in
+// c->part_alt (the force kernels write there; the slices are then moved to
+// input order in c->part).
+static int ensure_part(nbody_ctx *c, int S) {
+  int rc = ensure_slices(c, &c->part, &c->part_slices, S);
+  if (!rc && c->order) rc = ensure_slices(c, &c->part_alt, &c->alt_slices, S);
+  return rc;
+}
+
+// The force kernels' output slices for this evaluation.
+static void *force_out(const nbody_ctx *c) { return c->order ? c->part_alt : c->part; }
 
 // Blocks (of sym_block_particles()) below which the automatic choice keeps
 // the one-sided kernel: with few blocks the diagonals hold too few work items
@@ -170,6 +191,7 @@ static bool use_sym(const nbody_ctx *c) {
 // pairs of distinct blocks, added over the block diagonals in order.  F64E
 // blocks are its float-float tiles.
 static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
+  void *out = force_out(c);
   const bool ff = c->mode == NBODY_F64E;
   const int B = sym_block(c);
   const int M = sym_blocks(c);
@@ -226,11 +248,11 @@ static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
     c->launches++;
   }
   CK(nb::launch_force_units(c->mode, posm_in, c->fpos, c->anchor, c->sym_units, (int64_t)M * P,
-                            ff ? nb::sym_r_ff() : nb::sym_r(), c->part, 0, c->st));
+                            ff ? nb::sym_r_ff() : nb::sym_r(), out, 0, c->st));
   c->launches++;
   S = P;
   if (nd == 0) return NBODY_OK;
-  nb::d4 *part = (nb::d4 *)c->part + (int64_t)(P - 1) * c->n;  // rows in slice P, columns in P + 1
+  nb::d4 *part = (nb::d4 *)out + (int64_t)(P - 1) * c->n;  // rows in slice P, columns in P + 1
   nb::d4 *rows = (nb::d4 *)c->sym_buf, *cols = rows + (int64_t)c->sym_d * c->n;
   for (int d0 = 1; d0 <= nd; d0 += c->sym_d) {
     const int D = std::min(c->sym_d, nd - d0 + 1);
@@ -247,9 +269,38 @@ static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
   return NBODY_OK;
 }
 
-// Raw force sums of the positions in posm_in into c->part; returns the number
-// of partial slices written through S.
+static int ensure_order(nbody_ctx *c) {
+  if (c->perm) return NBODY_OK;
+  if (cudaMalloc(&c->ord_scratch, nb::order_scratch_bytes(c->n)) != cudaSuccess ||
+      cudaMalloc(&c->perm, sizeof(int32_t) * c->n) != cudaSuccess ||
+      cudaMalloc(&c->sposm, sizeof(d4) * c->n) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(NBODY_ENOMEM, "spatial order buffers");
+  }
+  return NBODY_OK;
+}
+
+static int force_sums(nbody_ctx *c, const void *posm_in, int &S);
+
+// Raw force sums of the positions in posm_in into c->part (input order);
+// returns the number of partial slices written through S.  With the spatial
+// order the particles are sorted along a Morton curve first, the force
+// kernels run on the sorted copy, and their slices are scattered back.
 static int force(nbody_ctx *c, const void *posm_in, int &S) {
+  if (!c->order) return force_sums(c, posm_in, S);
+  int rc = ensure_order(c);
+  if (rc) return rc;
+  CK(nb::launch_spatial_order((const d4 *)posm_in, c->n, c->ord_scratch, c->perm, c->sposm, c->st));
+  c->launches += 4;
+  rc = force_sums(c, c->sposm, S);
+  if (rc) return rc;
+  CK(nb::launch_unpermute((const d4 *)c->part_alt, c->perm, S, c->n, (d4 *)c->part, c->st));
+  c->launches++;
+  return NBODY_OK;
+}
+
+// The force kernels on posm_in, partial slices into force_out(c).
+static int force_sums(nbody_ctx *c, const void *posm_in, int &S) {
   std::pair<cudaEvent_t, cudaEvent_t> *ev = nullptr;
   if (c->prof) {
     if (c->ev_used == c->ev_pool.size()) {
@@ -282,7 +333,7 @@ static int force(nbody_ctx *c, const void *posm_in, int &S) {
   in.n = c->n;
   in.eps2 = c->eps * c->eps;
   in.seg = seg;
-  in.part = c->part;
+  in.part = force_out(c);
   nb::Shape sh = c->shape;
   sh.s = S;
   if (ev) CK(cudaEventRecord(ev->first, c->st));
@@ -327,7 +378,8 @@ static void free_all(nbody_ctx *c) {
   c->ev_pool.clear();
   void *ptrs[] = {c->posm[0], c->posm[1], c->vel, c->vbar, c->acc, c->part, c->rk_vs, c->rk_sr,
                   c->rk_sv, c->tmp_posm, c->tmp_acc, c->fpos, c->anchor, c->diag_blocks,
-                  c->diag_out, c->d_flag, c->stage, c->sym_units, c->sym_buf};
+                  c->diag_out, c->d_flag, c->stage, c->sym_units, c->sym_buf,
+                  c->ord_scratch, c->perm, c->sposm, c->part_alt};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_diag) cudaFreeHost(c->h_diag);
@@ -398,6 +450,7 @@ int nbody_create(nbody_ctx **out, int64_t n, int mode, double eps, double G, voi
     return fail(NBODY_ENOMEM, "device state");
   }
   default_shape(c, c->shape, 0, 0);
+  c->order = mode == NBODY_MIXED ? 1 : 0;
   *out = c;
   return NBODY_OK;
 }
@@ -689,6 +742,22 @@ int nbody_set_symmetric(nbody_ctx *c, int mode) {
   if (mode == 1 && c->mode != NBODY_FP64 && c->mode != NBODY_F64E)
     return fail(NBODY_EINVAL, "each-pair-once path is FP64 and F64E only");
   c->sym = mode;
+  return NBODY_OK;
+}
+
+int nbody_set_order(nbody_ctx *c, int order) {
+  if (!c) return fail(NBODY_EINVAL, "NULL context");
+  if (order != NBODY_ORDER_INPUT && order != NBODY_ORDER_SPATIAL)
+    return fail(NBODY_EINVAL, "order must be NBODY_ORDER_INPUT or NBODY_ORDER_SPATIAL");
+  if (order == NBODY_ORDER_SPATIAL && c->mode == NBODY_FP32)
+    return fail(NBODY_EINVAL, "the spatial order is not offered in NBODY_FP32");
+  c->order = order;
+  return NBODY_OK;
+}
+
+int nbody_get_order(const nbody_ctx *c, int *order) {
+  if (!c || !order) return fail(NBODY_EINVAL, "NULL argument");
+  *order = c->order;
   return NBODY_OK;
 }
 

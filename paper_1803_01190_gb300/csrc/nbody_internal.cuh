@@ -142,6 +142,17 @@ cudaError_t launch_diag(int mode, const void *posm, const void *vel, const void 
                         double *blocks, int nblocks, double *out9, cudaStream_t st);
 int diag_blocks(int64_t n);
 
+// Spatial (Morton) order of the particles (order.cu).  launch_spatial_order
+// writes perm (sorted position -> input index) and sposm[s] = posm[perm[s]],
+// using `scratch` of order_scratch_bytes(n); launch_unpermute scatters S
+// slices of sorted partial sums back to input order: part[k n + perm[s]] =
+// sorted[k n + s].
+size_t order_scratch_bytes(int64_t n);
+cudaError_t launch_spatial_order(const d4 *posm, int64_t n, void *scratch, int32_t *perm,
+                                 d4 *sposm, cudaStream_t st);
+cudaError_t launch_unpermute(const d4 *sorted, const int32_t *perm, int S, int64_t n, d4 *part,
+                             cudaStream_t st);
+
 // Records the detail that nbody_last_error() returns on this thread and
 // returns `code` (api.cu); every entry point reports its failures through it.
 int record_error(int code, const char *what, cudaError_t ce = cudaSuccess);

@@ -430,6 +430,71 @@ def test_mixed_force_error(nb, n):
     assert rms <= 1e-6 and mx <= 2e-5 and pmx <= 1e-6
 
 
+def _mixed_error(nb, pos, mass, eps, rows, order="spatial"):
+    n = len(mass)
+    with nb.Simulation(n, "mixed", eps=eps) as sim:
+        sim.set_order(order)
+        acc, pot = sim.accel(pos, mass)
+    acc_o, pot_o, _ = oracle.accel(pos, mass, eps, rows=rows)
+    e = rel_errors(acc[rows], acc_o)
+    ep = np.abs(pot[rows] - pot_o) / np.abs(pot_o)
+    return float(np.sqrt((e ** 2).mean())), float(e.max()), float(ep.max())
+
+
+@pytest.mark.parametrize("n", [4099, 2 ** 16 + 3])
+@pytest.mark.parametrize("dist", ["uniform", "plummer"])
+@pytest.mark.parametrize("eps", [1e-3, 0.0])
+def test_mixed_force_error_small_softening(nb, n, dist, eps):
+    """Mixed mode with softening far below the mean separation (eps = 1e-3)
+    and none at all (eps = 0), lognormal masses, ragged sizes: RMS relative
+    acceleration error <= 1e-6 against the oracle (the bound the mixed mode
+    states), with the default spatial order.  In input order the same cases
+    reach ~1e-6 at N = 2^16 (the tiles span the whole cloud), printed for contrast."""
+    s = nbody_ics.SEED_BASE + 3
+    pos = (nbody_ics.uniform_sphere(n, s) if dist == "uniform" else nbody_ics.plummer(n, s))[0]
+    mass = nbody_ics.lognormal_masses(n, s + 1)
+    rows = np.sort(np.random.default_rng(n).choice(n, 384, replace=False))
+    rms, mx, pmx = _mixed_error(nb, pos, mass, eps, rows)
+    rms_in, _, _ = _mixed_error(nb, pos, mass, eps, rows, order="input")
+    print(f"mixed {dist} N={n} eps={eps}: spatial rms {rms:.2e} max {mx:.2e} pot {pmx:.2e}; "
+          f"input order rms {rms_in:.2e}")
+    assert rms <= 1e-6 and pmx <= 1e-6
+    if n > 2 ** 16:
+        assert rms < rms_in   # where tiles in input order span the cloud, the order pays
+
+
+def test_spatial_order_is_a_function_of_the_positions(nb):
+    """The spatial order depends on the positions only: permuting the input
+    permutes the mixed-mode result bit for bit (no two particles share a
+    Morton cell here), and repeated calls agree bit for bit."""
+    n = 20000
+    w = nbody_ics.workload("sweep_uniform", n=n)
+    perm = np.random.default_rng(5).permutation(n)
+    with nb.Simulation(n, "mixed", eps=1e-3) as sim:
+        assert sim.get_order() == "spatial"
+        a1, p1 = sim.accel(w["pos"], w["mass"])
+        a2, p2 = sim.accel(w["pos"][perm], w["mass"][perm])
+        a3, _ = sim.accel(w["pos"], w["mass"])
+    assert np.array_equal(a1[perm], a2) and np.array_equal(p1[perm], p2)
+    assert np.array_equal(a1, a3)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "f64e"])
+def test_spatial_order_in_binary64_modes(nb, mode):
+    """FP64 and F64E accept the spatial order (one-sided and each-pair-once
+    paths); results stay within the FP64 gate."""
+    for n in (3001, 64 * 512 + 13):
+        w = nbody_ics.workload("sweep_plummer", n=n)
+        rows = np.sort(np.random.default_rng(n).choice(n, 256, replace=False))
+        with nb.Simulation(n, mode, eps=w["eps"]) as sim:
+            sim.set_order("spatial")
+            acc, pot = sim.accel(w["pos"], w["mass"])
+        _check_fp64(acc, pot, w["pos"], w["mass"], w["eps"], rows=rows)
+    with nb.Simulation(10, "fp32", eps=0.01) as sim:
+        with pytest.raises(nb.NbodyError):
+            sim.set_order("spatial")
+
+
 @pytest.mark.parametrize("n", [1000, 2 ** 14 + 7])
 def test_fp32_force_error(nb, n):
     rms, mx, pmx = _measured(nb, "fp32", "disk_halo", n)
