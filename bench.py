@@ -544,6 +544,7 @@ def run_drift(args):
         curve = []
         t0 = time.perf_counter()
         done = 0
+        log = open(args.drift_out, "w") if args.drift_out else None
         while done < args.drift_steps:
             k = min(args.drift_every, args.drift_steps - done)
             sim.step(dt, k, scheme=args.drift_scheme)
@@ -551,6 +552,13 @@ def run_drift(args):
             d = sim.diagnostics()
             curve.append([done, d["E"] / d0["E"] - 1, float(np.linalg.norm(d["P"] - d0["P"])),
                           d["L"][2] / d0["L"][2] - 1])
+            if log:   # the curve so far survives an interrupted run
+                log.write(json.dumps({"step": done, "wall_s": time.perf_counter() - t0,
+                                      "dE_over_E0": curve[-1][1], "dP_abs": curve[-1][2],
+                                      "dLz_over_Lz0": curve[-1][3]}) + "\n")
+                log.flush()
+        if log:
+            log.close()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     c = np.array(curve)
@@ -653,6 +661,8 @@ def main():
     ap.add_argument("--evolution-out", default=None, help="npz file for the maps and curves")
     ap.add_argument("--drift-dt", type=float, default=DT)
     ap.add_argument("--drift-every", type=int, default=100)
+    ap.add_argument("--drift-out", default=None,
+                    help="--drift: also write each sample of the curve to this file as it is taken")
     ap.add_argument("--symmetric", type=int, choices=[-1, 0, 1], default=-1,
                     help="--profile-force: each-pair-once path -1 automatic, 0 off, 1 on")
     ap.add_argument("--profile-force", choices=["fp64", "f64e", "mixed", "fp32"], default=None,

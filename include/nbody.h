@@ -139,6 +139,21 @@ int nbody_accel(nbody_ctx *ctx, const double *pos, const double *mass, double *a
                 int on_device);
 
 /*
+ * Eq. 1-2 for the rows i in [i0, i0 + ni) only, against all n particles of
+ * pos (n x 3) and mass (n): acc (ni x 3) and pot (ni, may be NULL) for those
+ * rows, row k holding particle i0 + k.  This is the per-GPU share of the
+ * paper's i-partition of the force sum over k GPUs (section 2, Figs. 1-3:
+ * every GPU holds all positions and sums N/k particles).  It always uses the
+ * one-sided kernels in input order with the context's launch shape, so the
+ * rows equal, bit for bit, the same rows of nbody_accel on a context with the
+ * each-pair-once path off (nbody_set_symmetric 0) and NBODY_ORDER_INPUT.
+ * Does not touch the simulation state.  Synchronises.  Errors: EINVAL (NULL
+ * pos/mass/acc, i0 < 0, ni < 1, i0 + ni > n), ENOMEM, ECUDA.
+ */
+int nbody_accel_rows(nbody_ctx *ctx, int64_t i0, int64_t ni, const double *pos, const double *mass,
+                     double *acc, double *pot, int on_device);
+
+/*
  * Accelerations and potentials of the current state (those of the last force
  * evaluation at the state's positions, computed now if stale).  acc (n x 3),
  * pot (n); either may be NULL.  Synchronises.

@@ -171,6 +171,19 @@ class Simulation:
         check(lib.nbody_accel(self._h, pp, pm, pa, po, dev), "nbody_accel")
         return acc, pot
 
+    def accel_rows(self, i0, ni, pos, mass):
+        """Eq. 1-2 for the rows [i0, i0 + ni) against all n particles of pos and
+        mass: (acc (ni,3), pot (ni,)), where the inputs live."""
+        keep = []
+        pp, dev = _ptr_in(pos, (self.n, 3), keep)
+        pm, dm = _ptr_in(mass, (self.n,), keep)
+        if dm != dev:
+            raise ValueError("pos and mass must both be on the host or both on the device")
+        acc, pa = self._out((int(ni), 3), dev)
+        pot, po = self._out((int(ni),), dev)
+        check(lib.nbody_accel_rows(self._h, int(i0), int(ni), pp, pm, pa, po, dev), "nbody_accel_rows")
+        return acc, pot
+
     def get_accel(self, on_device=False):
         acc, pa = self._out((self.n, 3), on_device)
         pot, po = self._out((self.n,), on_device)

@@ -38,6 +38,7 @@ _SIGS = {
     "nbody_set_clock": (_i, [_vp, _d, _i64]),
     "nbody_accel": (_i, [_vp, _vp, _vp, _vp, _vp, _i]),
     "nbody_get_accel": (_i, [_vp, _vp, _vp, _i]),
+    "nbody_accel_rows": (_i, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i]),
     "nbody_step": (_i, [_vp, _i, _d, _i64]),
     "nbody_diagnostics": (_i, [_vp, _dp, _dp, _dp]),
     "nbody_diagnostics_ext": (_i, [_vp, _dp, _dp, _dp, _dp, _dp]),

@@ -191,7 +191,6 @@ static bool use_sym(const nbody_ctx *c) {
 // pairs of distinct blocks, added over the block diagonals in order.  F64E
 // blocks are its float-float tiles.
 static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
-  void *out = force_out(c);
   const bool ff = c->mode == NBODY_F64E;
   const int B = sym_block(c);
   const int M = sym_blocks(c);
@@ -208,6 +207,7 @@ static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
   while (P < want && P < (ff ? 2 : 4)) P *= 2;
   int rc = ensure_part(c, P + 2);
   if (rc) return rc;
+  void *out = force_out(c);  // only after ensure_part, which may (re)allocate it
   if (c->sym_units_m != M * P) {
     if (c->sym_units) cudaFree(c->sym_units);
     c->sym_units = nullptr;
@@ -555,15 +555,16 @@ int nbody_get_state(nbody_ctx *c, double *pos, double *vel, double *t, int64_t *
   return sync(c);
 }
 
-static int copy_acc_out(nbody_ctx *c, const void *accbuf, double *acc, double *pot, int on_device) {
-  const size_t n = (size_t)c->n;
+static int copy_acc_out(nbody_ctx *c, const void *accbuf, double *acc, double *pot, int on_device,
+                        int64_t count = -1) {
+  const size_t n = (size_t)(count < 0 ? c->n : count);
   if (on_device) {
-    CK(nb::launch_unpack_acc(c->mode, accbuf, c->n, acc, pot, c->st));
+    CK(nb::launch_unpack_acc(c->mode, accbuf, (int64_t)n, acc, pot, c->st));
     c->launches++;
   } else {
     int rc = ensure_stage(c);
     if (rc) return rc;
-    CK(nb::launch_unpack_acc(c->mode, accbuf, c->n, acc ? c->stage : nullptr,
+    CK(nb::launch_unpack_acc(c->mode, accbuf, (int64_t)n, acc ? c->stage : nullptr,
                              pot ? c->stage + 3 * n : nullptr, c->st));
     c->launches++;
     if (acc) CK(cudaMemcpyAsync(acc, c->stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -590,6 +591,51 @@ int nbody_accel(nbody_ctx *c, const double *pos, const double *mass, double *acc
   CK(nb::launch_store_acc(c->mode, epi(c, S), c->tmp_acc, c->st));
   c->launches++;
   return copy_acc_out(c, c->tmp_acc, acc, pot, on_device);
+}
+
+int nbody_accel_rows(nbody_ctx *c, int64_t i0, int64_t ni, const double *pos, const double *mass,
+                     double *acc, double *pot, int on_device) {
+  if (!c || !pos || !mass || !acc) return fail(NBODY_EINVAL, "NULL argument");
+  if (i0 < 0 || ni < 1 || i0 > c->n - ni) return fail(NBODY_EINVAL, "rows outside [0, n)");
+  CK(cudaSetDevice(c->device));
+  if (!c->tmp_posm) {
+    if (cudaMalloc(&c->tmp_posm, (size_t)c->n * r4(c)) != cudaSuccess ||
+        cudaMalloc(&c->tmp_acc, (size_t)c->n * r4(c)) != cudaSuccess)
+      return fail(NBODY_ENOMEM, "accel buffers");
+  }
+  nvtxRangePushA("nbody_accel_rows");
+  int rc = load_arrays(c, pos, nullptr, mass, on_device, c->tmp_posm, nullptr, false);
+  int S = 0;
+  const int64_t seg = seg_len(c, S);
+  if (!rc) rc = ensure_part(c, S);
+  nvtxRangePop();
+  if (rc) return rc;
+  // the one-sided kernels in input order, in the context's launch shape: the
+  // rows come out as those rows of nbody_accel with the each-pair-once path
+  // off and NBODY_ORDER_INPUT, bit for bit
+  if (c->mode == NBODY_MIXED || c->mode == NBODY_F64E) {
+    CK(nb::launch_mixed_prep((const d4 *)c->tmp_posm, c->n, c->shape.t, c->fpos, c->anchor, c->st,
+                             c->mode == NBODY_F64E));
+    c->launches++;
+  }
+  nb::ForceIn in;
+  in.posm = c->tmp_posm;
+  in.fpos = c->fpos;
+  in.anchor = c->anchor;
+  in.n = c->n;
+  in.eps2 = c->eps * c->eps;
+  in.seg = seg;
+  in.part = c->part;
+  in.i0 = i0;
+  in.rows = ni;
+  nb::Shape sh = c->shape;
+  sh.s = S;
+  CK(nb::launch_force(c->mode, in, sh, c->st));
+  nb::EpiIn e = epi(c, S);
+  e.n = ni;
+  CK(nb::launch_store_acc(c->mode, e, c->tmp_acc, c->st));
+  c->launches += 2;
+  return copy_acc_out(c, c->tmp_acc, acc, pot, on_device, ni);
 }
 
 int nbody_get_accel(nbody_ctx *c, double *acc, double *pot, int on_device) {

@@ -218,9 +218,11 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
 
 // ---------------------------------------------------------------- work descriptors
 // A kernel runs units k = first(), first() + stride(), ... < count().
-// Dense: one system of n particles; block (x, y) = i-block x against j-segment y.
+// Dense: one system of n particles; block (x, y) = i-block x of the rows
+// [i_base, i_base + rows) against j-segment y of all n; the row sums go to
+// part[y * rows + (i - i_base)] (all rows: i_base = 0, rows = n).
 struct DenseWork {
-  int64_t n, seg;
+  int64_t n, seg, i_base, rows;
   double eps2;
   int per_block, tile;
   __device__ __forceinline__ int64_t first() const { return 0; }
@@ -228,11 +230,12 @@ struct DenseWork {
   __device__ __forceinline__ int64_t count() const { return 1; }
   __device__ __forceinline__ Unit get(int64_t) const {
     Unit u;
-    u.i0 = (int64_t)blockIdx.x * per_block;
-    u.ni = (int)min((int64_t)per_block, n - u.i0);
+    const int64_t r0 = (int64_t)blockIdx.x * per_block;
+    u.i0 = i_base + r0;
+    u.ni = (int)min((int64_t)per_block, rows - r0);
     u.j0 = (int64_t)blockIdx.y * seg;
     u.nj = (int)min(seg, n - u.j0);
-    u.out = (int64_t)blockIdx.y * n + u.i0;
+    u.out = (int64_t)blockIdx.y * rows + r0;
     u.anchor = u.j0 / tile;
     u.eps2 = eps2;
     return u;
@@ -1416,13 +1419,17 @@ cudaError_t launch_sym_combine(const d4 *rows, const d4 *cols, int D, int64_t n,
 }
 
 cudaError_t launch_force(int mode, const ForceIn &in, const Shape &sh, cudaStream_t st) {
-  if (!shape_supported(mode, sh) || in.n < 1) return cudaErrorInvalidValue;
+  const int64_t rows = in.rows < 0 ? in.n : in.rows;
+  if (!shape_supported(mode, sh) || in.n < 1 || rows < 1 || in.i0 < 0 || in.i0 + rows > in.n)
+    return cudaErrorInvalidValue;
   const int64_t per_block = (int64_t)sh.bt * sh.r;
-  const int64_t gx = (in.n + per_block - 1) / per_block;
+  const int64_t gx = (rows + per_block - 1) / per_block;
   if (gx > 0x7fffffff) return cudaErrorInvalidValue;
   DenseWork w;
   w.n = in.n;
   w.seg = in.seg;
+  w.i_base = in.i0;
+  w.rows = rows;
   w.eps2 = in.eps2;
   w.per_block = (int)per_block;
   w.tile = sh.t;

@@ -74,7 +74,9 @@ struct ForceIn {
   int64_t n;
   double eps2;
   int64_t seg;           // j-segment length (multiple of the tile)
-  void *part;            // S * n entries
+  void *part;            // S * rows entries
+  int64_t i0 = 0;        // the rows [i0, i0 + rows) are summed against all n
+  int64_t rows = -1;     // -1: all n
 };
 
 // launchers (force.cu); return cudaError_t of the launch

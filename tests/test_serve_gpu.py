@@ -83,8 +83,8 @@ def test_batch_alone_equals_mix_bitwise(sv):
 
 def test_batch_matches_single_context(sv):
     """The same simulation through a batch and through a single context (other
-    launch shapes, so other rounding order): equal within 1e-12 (FP64) and
-    1e-9 (MIXED) relative after 10 steps."""
+    launch shapes, so other rounding order; both in input order): equal within
+    1e-12 (FP64) and 1e-9 (MIXED) relative after 10 steps."""
     nb, serve = sv
     p, v, m = _plummer(1500, 9)
     for mode, tol in (("fp64", 1e-12), ("mixed", 1e-9)):
@@ -94,6 +94,7 @@ def test_batch_matches_single_context(sv):
         bp, bv, _, _ = b.get_state(s)
         b.close()
         with nb.Simulation(1500, mode, eps=0.01) as sim:
+            sim.set_order("input")   # the pool sums in admission order
             sim.set_state(p, v, m)
             sim.step(1e-3, 10)
             sp, svv, _, _ = sim.get_state()
@@ -142,6 +143,7 @@ def test_server_continuous_batching_alone_vs_mix(sv):
     for rq in out["done"]:
         p, v, m = rq.make()
         with nb.Simulation(rq.n, rq.mode, eps=rq.eps, G=rq.G) as sim:
+            sim.set_order("input")   # the pool sums in admission order
             sim.set_state(p, v, m)
             sim.step(rq.dt, rq.nsteps)
             sp, svv, _, _ = sim.get_state()
