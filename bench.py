@@ -586,7 +586,7 @@ def run_evolution(args):
     modes = args.evolution.split(",")
     w = nbody_ics.workload("disk_halo", n=args.n)
     nd = args.n // 2                   # disk particles come first
-    edges = np.linspace(-6.0, 6.0, 129)
+    edges = np.linspace(-6.0, 6.0, args.evolution_grid + 1)
     area = (edges[1] - edges[0]) ** 2
     data, summary = {}, {}
     for mode in modes:
@@ -606,8 +606,13 @@ def run_evolution(args):
                 com.append((m[:, None] * pos).sum(0) / m.sum())
                 com_disk.append((m[:nd, None] * pos[:nd]).sum(0) / m[:nd].sum())
                 dP.append(float(np.linalg.norm(sim.diagnostics()["P"] - P0)))
-                h, _, _ = np.histogram2d(pos[:nd, 0], pos[:nd, 1], bins=[edges, edges], weights=m[:nd])
-                maps.append(h / area)
+                if args.evolution_counts:   # particles per cell (equal masses: sigma = counts m / area)
+                    h, _, _ = np.histogram2d(pos[:nd, 0], pos[:nd, 1], bins=[edges, edges])
+                    maps.append(h.astype(np.uint16))
+                else:
+                    h, _, _ = np.histogram2d(pos[:nd, 0], pos[:nd, 1], bins=[edges, edges],
+                                             weights=m[:nd])
+                    maps.append(h / area)
                 if done >= args.evolution_steps:
                     break
                 k = min(args.evolution_every, args.evolution_steps - done)
@@ -617,21 +622,23 @@ def run_evolution(args):
             wall = time.perf_counter() - t0
         com, com_disk, maps = np.array(com), np.array(com_disk), np.array(maps)
         data.update({f"{mode}_t": np.array(times), f"{mode}_com": com, f"{mode}_com_disk": com_disk,
-                     f"{mode}_dP": np.array(dP), f"{mode}_sigma": maps})
+                     f"{mode}_dP": np.array(dP),
+                     f"{mode}_counts" if args.evolution_counts else f"{mode}_sigma": maps})
         summary[mode] = {"wall_s": wall,
                          "max_dP_abs": float(max(dP)),
                          "max_dRcm": float(np.linalg.norm(com - com[0], axis=1).max()),
                          "max_dRcm_disk": float(np.linalg.norm(com_disk - com_disk[0], axis=1).max())}
     ref = modes[0]
+    key = "counts" if args.evolution_counts else "sigma"
     for mode in modes[1:]:
-        a, b = data[f"{ref}_sigma"], data[f"{mode}_sigma"]
+        a, b = data[f"{ref}_{key}"].astype(float), data[f"{mode}_{key}"].astype(float)
         summary[mode]["sigma_L1_diff_vs_" + ref] = [
             float(np.abs(a[k] - b[k]).sum() / a[k].sum()) for k in range(len(a))]
         summary[mode]["sigma_max_abs_diff_vs_" + ref] = [float(np.abs(a[k] - b[k]).max())
                                                          for k in range(len(a))]
     summary["times"] = data[f"{ref}_t"].tolist()
     if args.evolution_out:
-        np.savez_compressed(args.evolution_out, edges=edges, **data)
+        np.savez_compressed(args.evolution_out, edges=edges, particle_mass=w["mass"][0], **data)
     print(json.dumps({"evolution": modes, "n": args.n, "eps": EPS, "dt": DT,
                       "steps": args.evolution_steps, "every": args.evolution_every,
                       "workload": workload_desc(args.n), "out": args.evolution_out,
@@ -659,6 +666,9 @@ def main():
     ap.add_argument("--evolution-steps", type=int, default=20000)
     ap.add_argument("--evolution-every", type=int, default=2000)
     ap.add_argument("--evolution-out", default=None, help="npz file for the maps and curves")
+    ap.add_argument("--evolution-grid", type=int, default=128, help="surface-density cells per side")
+    ap.add_argument("--evolution-counts", action="store_true",
+                    help="store particles per cell (uint16) instead of surface densities")
     ap.add_argument("--drift-dt", type=float, default=DT)
     ap.add_argument("--drift-every", type=int, default=100)
     ap.add_argument("--drift-out", default=None,
