@@ -233,8 +233,8 @@ int nbody_get_symmetric(const nbody_ctx *ctx, int *mode, int *active);
  * FP64 and F64E accept either (the order changes only the summation order);
  * NBODY_FP32 keeps input order (the paper's SP).
  * Memory: the first force evaluation with the spatial order allocates about
- * 96 + 32 S bytes per particle (keys, permutation, sorted copies of the
- * positions and of the S partial-sum slices).
+ * 70 + 32 S bytes per particle (keys, indices, permutation, sort scratch and
+ * sorted copies of the positions and of the S partial-sum slices).
  * Errors: EINVAL (NULL context, unknown order, NBODY_ORDER_SPATIAL in FP32).
  */
 #define NBODY_ORDER_INPUT   0

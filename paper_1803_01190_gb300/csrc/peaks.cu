@@ -3,11 +3,12 @@
 // packed (FMA pipes), and the SFU reciprocal square root.  Each rate comes from
 // a kernel that runs only independent chains of that one instruction over a
 // full wave of resident blocks, timed with CUDA events; the SM clock of the
-// same run comes from the SMs' cycle counters (per SM, the span from the
-// first block's start to the last block's end on it; warps are not scheduled
-// fairly, so one block alone finishes early and would understate the span).  These are the
-// denominators of the force kernels' rooflines: a kernel bound by a pipe can
-// reach at most that pipe's rate divided by its instructions per interaction.
+// same run comes from the SMs' cycle counters (per SM, the span from the first
+// block's start to the last block's end on it: warps are not scheduled fairly,
+// so one block alone finishes early and would understate the span).  These
+// are the denominators of the force kernels' rooflines: a kernel bound by a
+// pipe can reach at most that pipe's rate divided by its instructions per
+// interaction.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -100,7 +101,8 @@ __global__ void __launch_bounds__(kThreads) k_rate_rsqrt(int iters, double *sink
 }  // namespace
 
 extern "C" int nbody_measure_pipes(double *out, int nout) {
-  if (!out || nout < NBODY_PIPE_FIELDS) return nb::record_error(NBODY_EINVAL, "out needs NBODY_PIPE_FIELDS doubles");
+  if (!out || nout < NBODY_PIPE_FIELDS)
+    return nb::record_error(NBODY_EINVAL, "out needs NBODY_PIPE_FIELDS doubles");
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
