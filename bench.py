@@ -98,8 +98,9 @@ def traffic_f64(n, sym=False):
 
 
 def workload_desc(n):
+    seed = 20180113 if n >= 2 ** 20 else 20180112   # nbody_ics.workload("disk_halo", n)
     return (f"exponential disk (Rd=1, Rmax=5, h=0.05, Q=1.2) + live Plummer halo (a=3), 1:1, "
-            f"N={n}, eps={EPS}, KDK dt={DT}, seed 20180113")
+            f"N={n}, eps={EPS}, KDK dt={DT}, seed {seed}")
 
 
 # ------------------------------------------------------------------ helpers
