@@ -37,9 +37,10 @@ EPS, DT = 0.02, 5e-4
 # (counted from the kernels' source, confirmed by ncu instruction counts):
 # FP64 pipe instructions of the binary64 paths: 9 one-sided (3 DADD, 3 DFMA for
 # |d|^2 + eps^2, 3 DFMA for the acceleration sums; the potential sum is an
-# integer add); 14 per pair evaluated once for both particles, i.e. 7 per
+# integer add); 13 per pair evaluated once for both particles (the row
+# potential sum an integer add, the column one a DADD), i.e. 6.5 per
 # interaction.
-FP64_INSTR_PER_INTERACTION = {False: 9, True: 7}
+FP64_INSTR_PER_INTERACTION = {False: 9, True: 6.5}
 # FP32 FMA-pipe lane operations: mixed 13 (3 differences, 3 FMAs for
 # |d|^2 + eps^2, m y, y^2, m y^3, 3 FMAs and 1 add into the sums; two j per
 # packed instruction); F64E float-float 162 one-sided, 112 per interaction
@@ -469,7 +470,7 @@ def roofline_fp64(n, sym, force_ms, step_ms, pipes):
             "instr_per_interaction": ipi,
             "traffic": traffic_f64(n, sym),
             "traffic_note": ("DRAM bytes per force evaluation from one full-size ncu capture: mostly the "
-                             "per-diagonal row/column slices of the each-pair-once schedule, O(N^2/512), far "
+                             "per-diagonal row/column slices of the each-pair-once schedule, O(N^2/384), far "
                              "above the O(N) algorithmic bytes but ~0.2% of HBM bandwidth over the evaluation"
                              if sym else
                              "DRAM bytes per force evaluation from one full-size ncu capture; the O(N) "

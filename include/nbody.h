@@ -206,7 +206,7 @@ int nbody_get_launch(nbody_ctx *ctx, int *ipt, int *jsplit, int *threads, int *t
  * particles (Newton's third law; the same terms with opposite signs, summed in
  * a different fixed order than the one-sided kernels, so results differ from
  * them by rounding only and stay deterministic).  Particles are cut into
- * blocks of 512 (FP64) or 256 (F64E).  mode = -1 (default): automatic, used
+ * blocks of 384 (FP64) or 256 (F64E).  mode = -1 (default): automatic, used
  * when n spans at least 64 blocks; 0: never; 1: whenever n spans at least 2
  * blocks.  The launch shape of nbody_set_launch does not apply to this path.
  * Memory: the first force evaluation on this path allocates the context's

@@ -167,8 +167,8 @@ static void *force_out(const nbody_ctx *c) { return c->order ? c->part_alt : c->
 
 // Blocks (of sym_block_particles()) below which the automatic choice keeps
 // the one-sided kernel: with few blocks the diagonals hold too few work items
-// to fill the GPU (measured on GB300: 43.6 against 55.9 Gint/s at 32 blocks,
-// N = 2^14; 68.5 against 56.6 at 64 blocks, N = 2^15).
+// to fill the GPU (measured on GB300 with blocks of 512: 43.6 against 55.9
+// Gint/s at 32 blocks, N = 2^14; 68.5 against 56.6 at 64 blocks, N = 2^15).
 static const int SYM_AUTO_MIN_BLOCKS = 64;
 
 static int sym_block(const nbody_ctx *c) {
@@ -198,9 +198,9 @@ static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
   // pairs inside the diagonal blocks: each block's j range in P parts (one
   // unit each, partial sums in slices 0..P-1) so that the one-sided launch has
   // at least two work items per resident block slot
+  const int ur = ff ? nb::sym_r_ff() : nb::sym_units_r();  // one-sided R covering a block
   const int per_sm_1 = nb::force_max_blocks_per_sm(c->mode, nb::Shape{nb::force_block_threads(c->mode),
-                                                                      ff ? nb::sym_r_ff() : nb::sym_r(),
-                                                                      nb::force_tile(c->mode), 1});
+                                                                      ur, nb::force_tile(c->mode), 1});
   const int64_t slots_1 = (int64_t)c->num_sms * std::max(1, per_sm_1);
   const int64_t want = (2 * slots_1 + M - 1) / M;
   int P = 1;  // a power of two dividing the block size
@@ -247,8 +247,8 @@ static int force_sym(nbody_ctx *c, const void *posm_in, int &S) {
                              c->anchor, c->st, true));
     c->launches++;
   }
-  CK(nb::launch_force_units(c->mode, posm_in, c->fpos, c->anchor, c->sym_units, (int64_t)M * P,
-                            ff ? nb::sym_r_ff() : nb::sym_r(), out, 0, c->st));
+  CK(nb::launch_force_units(c->mode, posm_in, c->fpos, c->anchor, c->sym_units, (int64_t)M * P, ur,
+                            out, 0, c->st));
   c->launches++;
   S = P;
   if (nd == 0) return NBODY_OK;

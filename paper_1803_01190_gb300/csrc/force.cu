@@ -24,9 +24,9 @@
 //         1/r^2 within 0.52 ulp (SFU seed, exact integer residual), the
 //         products m/r and (m/r)/r^2 by a correctly rounded integer binary64
 //         multiply, and the potential sum by a correctly rounded integer
-//         binary64 add.  From 64 blocks of 512 particles the FP64 path
+//         binary64 add.  From 64 blocks of 384 particles the FP64 path
 //         evaluates each pair once for both particles (k_force_f64_sym:
-//         14 FP64 instructions per pair, 7 per interaction).
+//         13 FP64 instructions per pair, 6.5 per interaction).
 //   mixed binary32 pair arithmetic (packed: two j per instruction, SFU
 //         reciprocal square root) on coordinates re-centred on an anchor (the
 //         per-coordinate median) per j-tile, with the i coordinates held as
@@ -357,8 +357,8 @@ __global__ void __launch_bounds__(BT) k_force_f64(const d4 *__restrict__ posm, W
 // ---------------------------------------------------------------- binary64, each pair once
 // Newton's third law: the pair (i, j) contributes m_j d / w to a_i and
 // -m_i d / w to a_j with the same d = r_j - r_i and w = (|d|^2 + eps^2)^{3/2},
-// so one evaluation of d, |d|^2 + eps^2, 1/r and 1/r^2 serves both: 14 FP64
-// instructions for two interactions instead of 20.
+// so one evaluation of d, |d|^2 + eps^2, 1/r and 1/r^2 serves both: 13 FP64
+// instructions for two interactions instead of 18 (the one-sided kernel's 9 twice).
 //
 // Particles are cut into M blocks of B = BT*R.  A work item (d, I), d >= 1,
 // pairs i-block I with j-block J = (I + d) mod M; d = 1 .. floor(M/2) covers
@@ -410,10 +410,13 @@ __device__ __forceinline__ void scale_pair(double m, const MassSig &ms, uint64_t
   }
 }
 
+// The row potential sum pt (a bit pattern) is added on the integer pipes
+// (acc_pos, bit-identical to DADD), the column one gp in binary64: 13 FP64
+// instructions per pair.
 __device__ __forceinline__ void body_f64_sym(const d4 &pj, const MassSig &mj, double xi,
                                              double yi, double zi, double mi,
                                              const MassSig &msi, double eps2, double &ax,
-                                             double &ay, double &az, double &pt, double &gx,
+                                             double &ay, double &az, uint64_t &pt, double &gx,
                                              double &gy, double &gz, double &gp) {
   const double dx = pj.x - xi, dy = pj.y - yi, dz = pj.z - zi;
   const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
@@ -435,7 +438,7 @@ __device__ __forceinline__ void body_f64_sym(const d4 &pj, const MassSig &mj, do
   ax = fma(dx, f, ax);
   ay = fma(dy, f, ay);
   az = fma(dz, f, az);
-  pt += my;
+  acc_pos(pt, my);
   gx = fma(-dx, fj, gx);
   gy = fma(-dy, fj, gy);
   gz = fma(-dz, fj, gz);
@@ -469,7 +472,8 @@ __global__ void __launch_bounds__(BT) k_force_f64_sym(const d4 *__restrict__ pos
     }
     return;
   }
-  double xi[R], yi[R], zi[R], mi[R], ax[R], ay[R], az[R], pt[R];
+  double xi[R], yi[R], zi[R], mi[R], ax[R], ay[R], az[R];
+  uint64_t pt[R];  // bit patterns of the row potential sums
   MassSig msi[R];
 #pragma unroll
   for (int r = 0; r < R; r++) {
@@ -479,7 +483,8 @@ __global__ void __launch_bounds__(BT) k_force_f64_sym(const d4 *__restrict__ pos
     zi[r] = p.z;
     mi[r] = p.w;
     msi[r] = mass_sig(p.w);
-    ax[r] = ay[r] = az[r] = pt[r] = 0.0;
+    ax[r] = ay[r] = az[r] = 0.0;
+    pt[r] = 0;
   }
   for (int t0 = 0; t0 < B; t0 += T) {
     const int64_t jt = j0 + t0;
@@ -522,7 +527,7 @@ __global__ void __launch_bounds__(BT) k_force_f64_sym(const d4 *__restrict__ pos
 #pragma unroll
   for (int r = 0; r < R; r++) {
     const int64_t i = i0 + r * BT + tid;
-    if (i < n) rowo[i] = d4{ax[r], ay[r], az[r], pt[r]};
+    if (i < n) rowo[i] = d4{ax[r], ay[r], az[r], __longlong_as_double((long long)pt[r])};
   }
 }
 
@@ -1370,10 +1375,17 @@ static cudaError_t launch_w(int mode, int r, const void *posm, const float4 *fpo
 }
 
 // ---------------------------------------------------------------- binary64, each pair once: launches
-constexpr int SYM_BT = 128, SYM_R = 4, SYM_T = 128;
+// R = 3 (blocks of 384): 114 registers, 4 blocks of 4 warps per SM; measured on
+// GB300 at N = 2^18 (this kernel alone): R = 4 (148 registers, 3 blocks) 78.9,
+// R = 3 81.6, R = 2 78.8 Gint/s with both potential sums in binary64; with the
+// row sum on the integer pipes R = 4 73.3, R = 3 85.6, R = 2 83.4.
+constexpr int SYM_BT = 128, SYM_R = 3, SYM_T = 128;
 
 int sym_block_particles() { return SYM_BT * SYM_R; }
 int sym_r() { return SYM_R; }
+// the one-sided kernel's R for the pairs inside the diagonal blocks: the
+// smallest supported R whose BT*R covers a block
+int sym_units_r() { return SYM_R <= 1 ? 1 : SYM_R <= 2 ? 2 : SYM_R <= 4 ? 4 : 8; }
 
 int sym_blocks_per_sm() {
   int nb = 0;

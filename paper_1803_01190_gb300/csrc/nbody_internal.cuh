@@ -95,12 +95,14 @@ cudaError_t launch_mixed_prep(const d4 *posm, int64_t n, int tile, float4 *fpos,
                               cudaStream_t st, bool ff = false);
 int force_max_blocks_per_sm(int mode, const Shape &sh);
 // FP64, each pair once (Newton's third law): blocks of sym_block_particles()
-// particles; launch D diagonals d0 .. d0+D-1 of the M x M block pairs, row
+// particles (the one-sided kernel with R = sym_units_r() runs the pairs inside
+// each block); launch D diagonals d0 .. d0+D-1 of the M x M block pairs, row
 // sums of diagonal d0+k into rows[k*n ..], column sums into cols[k*n ..];
 // launch_sym_combine adds them (in diagonal order) into acc_rows / acc_cols
 // (overwriting them when first).
 int sym_block_particles();
 int sym_r();
+int sym_units_r();
 int sym_blocks_per_sm();
 cudaError_t launch_force_f64_sym(const d4 *posm, int64_t n, double eps2, int M, int d0, int D,
                                  d4 *rows, d4 *cols, cudaStream_t st);

@@ -126,9 +126,9 @@ def test_golden_fixture(nb):
 
 
 # ------------------------------------------------------------------ FP64, each pair once
-# 512-particle blocks: n = 513, 1024 (M = 2: the half diagonal d = M/2), 1100 (M = 3),
-# 1537 (M = 4), 2559 (M = 5), 4099 (M = 9, ragged tail of 3)
-@pytest.mark.parametrize("n", [513, 1024, 1100, 1537, 2559, 4099])
+# 384-particle blocks: n = 385 and 768 (M = 2: the half diagonal d = M/2; a tail of one, two full
+# blocks), 1100 (M = 3), 1537 (M = 5, tail of one), 2559 (M = 7), 4099 (M = 11, ragged tail of 259)
+@pytest.mark.parametrize("n", [385, 768, 1100, 1537, 2559, 4099])
 @pytest.mark.parametrize("eps", [0.01, 0.0])
 def test_fp64_symmetric_accel_sizes(nb, n, eps):
     pos, _, _ = nbody_ics.plummer(n, 31 + n)
@@ -180,7 +180,7 @@ def test_f64e_symmetric_against_one_sided_and_kdk(nb):
 
 @pytest.mark.parametrize("mode", ["fp64", "f64e"])
 def test_symmetric_many_blocks_sampled(nb, mode):
-    """N = 2^18 + 77: 513 FP64 blocks (1025 F64E tiles), several launch groups
+    """N = 2^18 + 77: 683 FP64 blocks (1025 F64E tiles), several launch groups
     of block diagonals, diagonal blocks split into parts, ragged tail; sampled
     particles from every block against the oracle."""
     n = 2 ** 18 + 77
@@ -196,7 +196,7 @@ def test_symmetric_many_blocks_sampled(nb, mode):
 def test_fp64_symmetric_auto_and_off(nb):
     w = nbody_ics.workload("disk_halo", n=40000)
     with nb.Simulation(40000, "fp64", eps=w["eps"]) as sim:
-        assert sim.get_symmetric() == (-1, True)      # 79 blocks: automatic choice takes it
+        assert sim.get_symmetric() == (-1, True)      # 105 blocks: automatic choice takes it
         acc_s, pot_s = sim.accel(w["pos"], w["mass"])
         acc_s2, pot_s2 = sim.accel(w["pos"], w["mass"])
         sim.set_symmetric(0)
@@ -207,7 +207,7 @@ def test_fp64_symmetric_auto_and_off(nb):
     _check_fp64(acc_s, pot_s, w["pos"], w["mass"], w["eps"], rows=np.arange(0, 40000, 97))
     _check_fp64(acc_o, pot_o, w["pos"], w["mass"], w["eps"], rows=np.arange(0, 40000, 97))
     with nb.Simulation(20000, "fp64", eps=0.01) as small:
-        assert small.get_symmetric() == (-1, False)   # 40 blocks: one-sided kernel
+        assert small.get_symmetric() == (-1, False)   # 53 blocks: one-sided kernel
     with nb.Simulation(3000, "mixed", eps=0.01) as other:
         assert other.get_symmetric() == (-1, False)
         with pytest.raises(nb.NbodyError):
