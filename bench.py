@@ -37,10 +37,9 @@ EPS, DT = 0.02, 5e-4
 # (counted from the kernels' source, confirmed by ncu instruction counts):
 # FP64 pipe instructions of the binary64 paths: 9 one-sided (3 DADD, 3 DFMA for
 # |d|^2 + eps^2, 3 DFMA for the acceleration sums; the potential sum is an
-# integer add); 13 per pair evaluated once for both particles (the row
-# potential sum an integer add, the column one a DADD), i.e. 6.5 per
-# interaction.
-FP64_INSTR_PER_INTERACTION = {False: 9, True: 6.5}
+# integer add); 12 per pair evaluated once for both particles (both potential
+# sums integer adds), i.e. 6 per interaction.
+FP64_INSTR_PER_INTERACTION = {False: 9, True: 6}
 # FP32 FMA-pipe lane operations: mixed 13 (3 differences, 3 FMAs for
 # |d|^2 + eps^2, m y, y^2, m y^3, 3 FMAs and 1 add into the sums; two j per
 # packed instruction); F64E float-float 162 one-sided, 112 per interaction

@@ -26,7 +26,7 @@
 //         multiply, and the potential sum by a correctly rounded integer
 //         binary64 add.  From 64 blocks of 384 particles the FP64 path
 //         evaluates each pair once for both particles (k_force_f64_sym:
-//         13 FP64 instructions per pair, 6.5 per interaction).
+//         12 FP64 instructions per pair, 6 per interaction).
 //   mixed binary32 pair arithmetic (packed: two j per instruction, SFU
 //         reciprocal square root) on coordinates re-centred on an anchor (the
 //         per-coordinate median) per j-tile, with the i coordinates held as
@@ -162,10 +162,11 @@ __device__ __forceinline__ double pack_f64(uint64_t sig, int e) {
 // one shifted right by the exponent difference with a sticky bit, at most a
 // one-bit normalisation after a carry, rounded at bit 10.  ok = false for a
 // subnormal or overflowing result or a negative operand, where the caller adds
-// in binary64 out of line.  It costs about 40 ALU-pipe instructions, a little
-// more than the FP64 pipe time of one DADD is worth in the one-sided kernel's
-// spare ALU capacity (measured +12 %), and less than nothing in the each-pair-
-// once kernel, whose second potential sum would need it twice (measured -15 %).
+// in binary64 out of line.  It costs about 40 ALU-pipe instructions, less ALU
+// time than the FP64 pipe time of one DADD (one FP64 instruction takes the
+// pipe as long as 32 ALU instructions): +12 % measured in the one-sided
+// kernel, and in the each-pair-once kernel, for both of its potential sums,
+// +22 % together with the block shape that makes room for the registers.
 __device__ __forceinline__ uint64_t add_pos_bits(uint64_t a, uint64_t b, bool &ok) {
   const uint64_t M52 = 0xFFFFFFFFFFFFFull;
   const bool sw = b > a;
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(BT) k_force_f64(const d4 *__restrict__ posm, W
 // ---------------------------------------------------------------- binary64, each pair once
 // Newton's third law: the pair (i, j) contributes m_j d / w to a_i and
 // -m_i d / w to a_j with the same d = r_j - r_i and w = (|d|^2 + eps^2)^{3/2},
-// so one evaluation of d, |d|^2 + eps^2, 1/r and 1/r^2 serves both: 13 FP64
+// so one evaluation of d, |d|^2 + eps^2, 1/r and 1/r^2 serves both: 12 FP64
 // instructions for two interactions instead of 18 (the one-sided kernel's 9 twice).
 //
 // Particles are cut into M blocks of B = BT*R.  A work item (d, I), d >= 1,
@@ -410,14 +411,14 @@ __device__ __forceinline__ void scale_pair(double m, const MassSig &ms, uint64_t
   }
 }
 
-// The row potential sum pt (a bit pattern) is added on the integer pipes
-// (acc_pos, bit-identical to DADD), the column one gp in binary64: 13 FP64
-// instructions per pair.
+// Both potential sums, pt (row) and gp (column), are bit patterns added on the
+// integer pipes (acc_pos, bit-identical to DADD): 12 FP64 instructions per
+// pair, 6 per interaction.
 __device__ __forceinline__ void body_f64_sym(const d4 &pj, const MassSig &mj, double xi,
                                              double yi, double zi, double mi,
                                              const MassSig &msi, double eps2, double &ax,
                                              double &ay, double &az, uint64_t &pt, double &gx,
-                                             double &gy, double &gz, double &gp) {
+                                             double &gy, double &gz, uint64_t &gp) {
   const double dx = pj.x - xi, dy = pj.y - yi, dz = pj.z - zi;
   const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
   const unsigned hi = (unsigned)__double2hiint(r2);
@@ -442,7 +443,7 @@ __device__ __forceinline__ void body_f64_sym(const d4 &pj, const MassSig &mj, do
   gx = fma(-dx, fj, gx);
   gy = fma(-dy, fj, gy);
   gz = fma(-dz, fj, gz);
-  gp += myj;
+  acc_pos(gp, myj);
 }
 
 // Padding beyond n: massless and far away (finite r^2, zero contribution).
@@ -493,8 +494,10 @@ __global__ void __launch_bounds__(BT) k_force_f64_sym(const d4 *__restrict__ pos
     __syncthreads();
 #pragma unroll 1
     for (int c = 0; c < T; c += 32) {
-      double gx = 0.0, gy = 0.0, gz = 0.0, gp = 0.0;
-#pragma unroll 2
+      double gx = 0.0, gy = 0.0, gz = 0.0;
+      uint64_t gp = 0;  // bit pattern of the column potential sum
+      // not unrolled: measured on GB300 at N = 2^18, unroll 2 ran 4 % slower
+#pragma unroll 1
       for (int k = 0; k < 32; k++) {
         const d4 pj = tile[c + ((lane + k) & 31)];
         const MassSig mj = mass_sig(pj.w);
@@ -508,7 +511,7 @@ __global__ void __launch_bounds__(BT) k_force_f64_sym(const d4 *__restrict__ pos
         gz = __shfl_sync(0xFFFFFFFFu, gz, src);
         gp = __shfl_sync(0xFFFFFFFFu, gp, src);
       }
-      colw[warp][c + lane] = d4{gx, gy, gz, gp};
+      colw[warp][c + lane] = d4{gx, gy, gz, __longlong_as_double((long long)gp)};
     }
     __syncthreads();
     {
@@ -1375,10 +1378,12 @@ static cudaError_t launch_w(int mode, int r, const void *posm, const float4 *fpo
 }
 
 // ---------------------------------------------------------------- binary64, each pair once: launches
-// R = 3 (blocks of 384): 114 registers, 4 blocks of 4 warps per SM; measured on
-// GB300 at N = 2^18 (this kernel alone): R = 4 (148 registers, 3 blocks) 78.9,
-// R = 3 81.6, R = 2 78.8 Gint/s with both potential sums in binary64; with the
-// row sum on the integer pipes R = 4 73.3, R = 3 85.6, R = 2 83.4.
+// R = 3 (blocks of 384): 114 registers, 4 blocks of 4 warps per SM.  Measured on
+// GB300 at N = 2^18 (this kernel alone, Gint/s): both potential sums in binary64
+// R = 4 (148 registers, 3 blocks) 78.9, R = 3 81.6, R = 2 78.8; the row sum on the
+// integer pipes R = 4 73.3, R = 3 85.6, R = 2 83.4; both sums on the integer
+// pipes, k-loop not unrolled: R = 3 96.1, R = 2 96.3, R = 1 95.3 (unrolled twice:
+// R = 2 92.2).
 constexpr int SYM_BT = 128, SYM_R = 3, SYM_T = 128;
 
 int sym_block_particles() { return SYM_BT * SYM_R; }
