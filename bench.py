@@ -55,11 +55,12 @@ F64E_LANEOPS_PER_INTERACTION = {False: 162, True: 112}
 # that was captured: `src_sha` hashes rsqrt_recip_sig, mul_sig, body_f64 and
 # k_force_f64.
 TRAFFIC = {"k_force_f64": {"bytes": 47.05e6 + 62.96e6, "n": 2 ** 20, "src_sha": "01dc06074becbf43"},
-           # each pair once: per force evaluation (1 one-sided launch on the diagonal
-           # blocks + 128 x (pair launch + combine launch)), from the first launch of
-           # each kernel in one capture
-           "k_force_f64_sym": {"bytes": 34.22e6 + 128 * (703.07e6 + 589.66e6), "n": 2 ** 20,
-                               "src_sha": "67da7c2abed4b181"}}
+           # each pair once, blocks of 384: per force evaluation 1 one-sided launch on the
+           # 2731 diagonal blocks + 1365 block diagonals in launches of 8 (pair kernel and
+           # combine); bytes of the first launch of each kernel in one full-size capture,
+           # the pair and combine launches scaled by 1365 / 8
+           "k_force_f64_sym": {"bytes": 34.00e6 + 1365 / 8 * (679.80e6 + 589.80e6), "n": 2 ** 20,
+                               "src_sha": "39fcfb6aac42cd11"}}
 
 
 def _kernel_src_sha(names):
@@ -84,6 +85,8 @@ def traffic_f64(n, sym=False):
         t = TRAFFIC["k_force_f64_sym"]
         sha = _kernel_src_sha(["__device__ __forceinline__ void rsqrt_recip_sig(",
                                "__device__ __forceinline__ uint64_t mul_sig(",
+                               "__device__ __forceinline__ uint64_t add_pos_bits(",
+                               "__device__ __forceinline__ void acc_pos(",
                                "__device__ __forceinline__ void scale_pair(",
                                "__device__ __forceinline__ void body_f64_sym(",
                                "__global__ void __launch_bounds__(BT) k_force_f64_sym(",
@@ -470,7 +473,7 @@ def roofline_fp64(n, sym, force_ms, step_ms, pipes):
             "traffic": traffic_f64(n, sym),
             "traffic_note": ("DRAM bytes per force evaluation from one full-size ncu capture: mostly the "
                              "per-diagonal row/column slices of the each-pair-once schedule, O(N^2/384), far "
-                             "above the O(N) algorithmic bytes but ~0.2% of HBM bandwidth over the evaluation"
+                             "above the O(N) algorithmic bytes but ~0.3% of HBM bandwidth over the evaluation"
                              if sym else
                              "DRAM bytes per force evaluation from one full-size ncu capture; the O(N) "
                              "algorithmic bytes (32 B in + partial sums out per particle) mostly stay in L2"),
