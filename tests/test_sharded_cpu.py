@@ -58,7 +58,7 @@ def _worker(rank, world, port, n, q):
     q.put((rank, gathered))
 
 
-@pytest.mark.parametrize("world,n", [(2, 1001), (3, 640)])
+@pytest.mark.parametrize("world,n", [(2, 1001), (3, 640), (3, 2)])
 def test_sharded_rows_equal_single_process(world, n):
     import torch.multiprocessing as mp
     import nbody_ics
