@@ -229,9 +229,10 @@ int nbody_get_symmetric(const nbody_ctx *ctx, int *mode, int *active);
  * reproducible bit for bit.  It matters for NBODY_MIXED: the binary32
  * coordinates relative to a j-tile's anchor keep their digits only when the
  * tile is spatially compact (force error at eps = 1e-3 several times
- * smaller), and it is the default there; NBODY_ORDER_INPUT elsewhere.
- * FP64 and F64E accept either (the order changes only the summation order);
- * NBODY_FP32 keeps input order (the paper's SP).
+ * smaller); NBODY_F64E gains less (its float-float coordinates lose digits
+ * only far from the anchor).  It is the default in both; NBODY_ORDER_INPUT in
+ * NBODY_FP64 (which accepts either: the order changes only its summation
+ * order).  NBODY_FP32 keeps input order (the paper's SP).
  * Memory: the first force evaluation with the spatial order allocates about
  * 70 + 32 S bytes per particle (keys, indices, permutation, sort scratch and
  * sorted copies of the positions and of the S partial-sum slices).

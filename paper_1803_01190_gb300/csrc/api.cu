@@ -450,7 +450,7 @@ int nbody_create(nbody_ctx **out, int64_t n, int mode, double eps, double G, voi
     return fail(NBODY_ENOMEM, "device state");
   }
   default_shape(c, c->shape, 0, 0);
-  c->order = mode == NBODY_MIXED ? 1 : 0;
+  c->order = (mode == NBODY_MIXED || mode == NBODY_F64E) ? 1 : 0;
   *out = c;
   return NBODY_OK;
 }
